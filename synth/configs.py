@@ -1,0 +1,156 @@
+"""The synthetic workloads (inputs only).
+
+make_config1: one detector, 32 s at 512 Hz (N = 16384), 64 TaylorF2 templates
+    with m1, m2 ~ U(1.4, 10), template 17 injected (circularly, at sample N/2)
+    at optimal SNR 12, threshold 5.5, 1 s clustering windows.
+make_config2: two detectors, 512 s at 2048 Hz (N = 2^20), 20 sine-Gaussian
+    glitches per detector, 50 TaylorF2 injections at SNR 6-20, a 2,000-template
+    coarse bank for stage 1 at 512 Hz and a 20,000-template fine bank for
+    stage 2 at 2048 Hz with its neighbourhood map (match >= 0.9).
+    ``small=True`` gives a scaled-down copy (32 s, 48 coarse, 480 fine) with
+    the same structure, for tests the oracle finishes in seconds.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import generators as g
+
+
+@dataclass
+class Config1:
+    n: int
+    fs: float
+    f_low: float
+    f_high: float
+    thr: float
+    window: int
+    psd: np.ndarray
+    m1: np.ndarray
+    m2: np.ndarray
+    inj_tmpl: int
+    inj_snr: float
+    inj_sample: int
+    inj_amp: float
+    noise_fd: np.ndarray          # complex128 [N/2+1]
+    signal_fd: np.ndarray         # complex128 [N/2+1], the injected signal alone
+    strain: np.ndarray            # float32 [1, N]
+
+    def bank(self, dtype=np.complex64):
+        return np.stack([g.taylorf2(self.n, self.fs, a, b, self.f_low, dtype=dtype)
+                         for a, b in zip(self.m1, self.m2)])
+
+
+def make_config1(seed=0, n=16384, fs=512.0, n_tmpl=64, inj_tmpl=17, inj_snr=12.0,
+                 f_low=30.0, thr=5.5):
+    rng = np.random.default_rng(seed)
+    noise = g.coloured_noise_fd(rng, n, fs)
+    m1, m2 = g.sample_bank_uniform_masses(rng, n_tmpl, 1.4, 10.0)
+    j0 = n // 2
+    amp = inj_snr / g.taylorf2_norm_continuum(m1[inj_tmpl], m2[inj_tmpl], f_low, fs / 2)
+    h = g.taylorf2(n, fs, m1[inj_tmpl], m2[inj_tmpl], f_low)
+    k = np.arange(n // 2 + 1)
+    sig = amp * h * np.exp(-2j * math.pi * k * j0 / n)
+    strain = g.strain_from_fd(noise + sig, n, fs).astype(np.float32)[None, :]
+    return Config1(n=n, fs=fs, f_low=f_low, f_high=fs / 2, thr=thr, window=int(round(fs)),
+                   psd=g.psd_bins(n, fs), m1=m1, m2=m2, inj_tmpl=inj_tmpl, inj_snr=inj_snr,
+                   inj_sample=j0, inj_amp=amp, noise_fd=noise, signal_fd=sig, strain=strain)
+
+
+@dataclass
+class Config2:
+    n2: int
+    fs2: float
+    n1: int
+    fs1: float
+    f_low: float
+    thr1: float
+    thr2: float
+    window1: int
+    window2: int
+    shift_s: float
+    n_shifts: int
+    coinc_s: float
+    rho_c_thr: float
+    psd1: np.ndarray
+    psd2: np.ndarray
+    coarse_m1: np.ndarray
+    coarse_m2: np.ndarray
+    fine_m1: np.ndarray
+    fine_m2: np.ndarray
+    nbhd_ptr: np.ndarray
+    nbhd_idx: np.ndarray
+    nbhd_match: np.ndarray
+    strain: np.ndarray            # float32 [2, n2]
+    injections: dict = field(default_factory=dict)
+    glitches: dict = field(default_factory=dict)
+
+    def coarse_bank(self, ids=None, dtype=np.complex64):
+        ids = range(len(self.coarse_m1)) if ids is None else ids
+        return np.stack([g.taylorf2(self.n1, self.fs1, self.coarse_m1[i], self.coarse_m2[i], self.f_low,
+                                    dtype=dtype) for i in ids])
+
+    def fine_bank(self, ids=None, dtype=np.complex64):
+        ids = range(len(self.fine_m1)) if ids is None else ids
+        return np.stack([g.taylorf2(self.n2, self.fs2, self.fine_m1[i], self.fine_m2[i], self.f_low,
+                                    dtype=dtype) for i in ids])
+
+
+def make_config2(seed=1, small=False):
+    if small:
+        T, n_coarse, n_fine, n_glitch, n_inj, n_shifts, min_match = 32.0, 48, 480, 4, 4, 5, 0.5
+    else:
+        T, n_coarse, n_fine, n_glitch, n_inj, n_shifts, min_match = 512.0, 2000, 20000, 20, 50, 101, 0.9
+    fs2, fs1, f_low = 2048.0, 512.0, 30.0
+    n2 = int(T * fs2)
+    n1 = int(T * fs1)
+    rng = np.random.default_rng(seed)
+    # banks: random in the chirp-time plane, chirp mass 1.2-10
+    cm1, cm2, _, _ = g.sample_bank_chirp_times(rng, n_coarse, f_low)
+    fm1, fm2, _, _ = g.sample_bank_chirp_times(rng, n_fine, f_low)
+    ptr, idx, val = g.nbhd_map(cm1, cm2, fm1, fm2, f_low, f_low, fs2 / 2, min_match=min_match)
+    # noise
+    nb = n2 // 2 + 1
+    fd = np.stack([g.coloured_noise_fd(rng, n2, fs2) for _ in range(2)])
+    # injections (same optimal SNR in both detectors, independent phases, dt_HL within 10 ms)
+    im1, im2, _, _ = g.sample_bank_chirp_times(rng, n_inj, f_low)
+    snr = rng.uniform(6.0, 20.0, n_inj)
+    slot = T / n_inj
+    tc = (np.arange(n_inj) + 0.5) * slot + rng.uniform(-0.25, 0.25, n_inj) * slot
+    dt_hl = rng.uniform(-0.010, 0.010, n_inj)
+    phi = rng.uniform(0, 2 * math.pi, (n_inj, 2))
+    amp = np.array([snr[i] / g.taylorf2_norm_continuum(im1[i], im2[i], f_low, fs2 / 2) for i in range(n_inj)])
+    for i in range(n_inj):
+        for d in range(2):
+            t0 = tc[i] + (dt_hl[i] if d == 1 else 0.0)
+            fd[d] += g.taylorf2(n2, fs2, im1[i], im2[i], f_low, t0=t0, phi0=phi[i, d], amp=amp[i])
+    strain = np.stack([g.strain_from_fd(fd[d], n2, fs2) for d in range(2)])
+    # glitches (time domain)
+    t = np.arange(n2) / fs2
+    gl = dict(det=[], t0=[], f0=[], Q=[], snr=[])
+    for d in range(2):
+        for _ in range(n_glitch):
+            f0 = rng.uniform(30.0, 500.0)
+            Q = rng.uniform(5.0, 20.0)
+            s = rng.uniform(8.0, 50.0)
+            t0 = rng.uniform(1.0, T - 1.0)
+            ph = rng.uniform(0, 2 * math.pi)
+            a = g.sine_gaussian_amplitude(s, f0, Q)
+            tau = Q / (math.sqrt(2.0) * math.pi * f0)
+            lo = max(0, int((t0 - 6 * tau) * fs2))
+            hi = min(n2, int((t0 + 6 * tau) * fs2) + 1)
+            strain[d, lo:hi] += g.sine_gaussian(t[lo:hi], t0, f0, Q, a, ph)
+            for key, v in zip(("det", "t0", "f0", "Q", "snr"), (d, t0, f0, Q, s)):
+                gl[key].append(v)
+    inj = dict(m1=im1, m2=im2, snr=snr, tc=tc, dt_hl=dt_hl, phi=phi, amp=amp)
+    return Config2(n2=n2, fs2=fs2, n1=n1, fs1=fs1, f_low=f_low, thr1=3.5, thr2=4.0,
+                   window1=int(fs1), window2=int(fs2), shift_s=5.0, n_shifts=n_shifts,
+                   coinc_s=0.015, rho_c_thr=7.0, psd1=g.psd_bins(n1, fs1), psd2=g.psd_bins(n2, fs2),
+                   coarse_m1=cm1, coarse_m2=cm2, fine_m1=fm1, fine_m2=fm2,
+                   nbhd_ptr=ptr, nbhd_idx=idx, nbhd_match=val,
+                   strain=strain.astype(np.float32), injections=inj,
+                   glitches={k: np.asarray(v) for k, v in gl.items()})
