@@ -1,0 +1,218 @@
+/*
+ * libmf - GB300 (sm_103a) hot path of a two-stage hierarchical matched-filter
+ * search for compact-binary gravitational-wave signals.
+ *
+ * Plain C ABI: opaque handles, plain pointers and sizes, no exceptions.  Every
+ * call returns an mf_status; on failure mf_last_error(plan) describes it.
+ * "device" pointers are CUDA global-memory addresses of the current device
+ * (e.g. torch.Tensor.data_ptr() of a CUDA tensor); "host" pointers are CPU
+ * memory.  Unless stated otherwise the caller owns every buffer it passes and
+ * the library copies what it keeps.  Work is enqueued asynchronously on the
+ * plan's CUDA stream; calls that return data to the host synchronise it.
+ * A plan is not thread-safe: use one plan per host thread.
+ *
+ * Conventions (shared with the documentation of every call):
+ *   N = FFT length (samples per segment), fs = sampling rate, dt = 1/fs,
+ *   df = fs/N, one-sided frequency bins k = 0..N/2 (nbins = N/2 + 1),
+ *   x~[k] = dt * sum_j x[j] exp(-2 pi i j k / N).
+ *   Complex arrays are interleaved (re, im) pairs: float32 pairs for MF_F32,
+ *   IEEE half pairs for MF_F16, bfloat16 pairs for MF_BF16.
+ */
+#ifndef MF_H_
+#define MF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_plan_s* mf_plan_t;
+
+typedef enum {
+  MF_OK = 0,
+  MF_EINVAL = 1,       /* bad argument (null pointer, size, unsupported N ...) */
+  MF_ENOMEM = 2,       /* device or host allocation failed */
+  MF_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  MF_ESTATE = 4,       /* call out of order (e.g. mf_filter before mf_set_psd) */
+  MF_EOVERFLOW = 5,    /* more results than the buffer holds; the count is still exact */
+  MF_ETIMEOUT = 6      /* a bounded device wait gave up (reported, never trapped) */
+} mf_status;
+
+typedef enum { MF_F32 = 0, MF_F16 = 1, MF_BF16 = 2 } mf_dtype;
+
+/* Plan description.  The matched filter of Eq. (1)-(2) (Sec. II) on segments
+ * of N samples: the analysis band is f_low <= f_k < f_high, 0 < k < N/2, and
+ * PSD bins that are positive and finite.  A trigger is kept when
+ * rho >= snr_thr (Sec. II, inclusive); one trigger per (detector, template,
+ * window of `window` samples aligned to sample 0), at the window's peak
+ * (ties: lowest sample).  Only samples in [valid_begin, valid_end) count. */
+typedef struct {
+  double fs;             /* sampling rate, Hz (> 0) */
+  int64_t n;             /* N, a power of two in [2^12, 2^20] */
+  int32_t n_det;         /* detectors, 1..8 */
+  double f_low, f_high;  /* band edges, Hz */
+  mf_dtype dtype;        /* storage type of the template bank */
+  double snr_thr;        /* rho threshold (> 0) */
+  int64_t window;        /* clustering window, samples, 1 <= window <= N */
+  int64_t valid_begin;   /* analysed range [valid_begin, valid_end), 0 <= b < e <= N */
+  int64_t valid_end;
+  int64_t max_triggers;  /* capacity of the device trigger buffer (>= 1) */
+  void* cuda_stream;     /* cudaStream_t to enqueue on; NULL = legacy default stream */
+} mf_plan_desc;
+
+/* One trigger: detector, template id, sample index of the window peak,
+ * rho at that sample and arg z (quantised to 2 pi / 2048). */
+typedef struct {
+  int32_t det;
+  int32_t tmpl;
+  int64_t sample;
+  float snr;
+  float phase;
+} mf_trigger;
+
+/* Create a plan (device buffers for the PSD weights and work space).
+ * *out is set only on MF_OK.  Errors: MF_EINVAL for an invalid desc. */
+mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc);
+
+/* Destroy a plan and free everything it owns (NULL is a no-op). */
+void mf_destroy(mf_plan_t plan);
+
+/* Message of the last failed call on this plan ("" if none).  Owned by the plan. */
+const char* mf_last_error(mf_plan_t plan);
+
+/* Set the one-sided PSD S_n(f_k) (Eq. 2), host float64 [nbins], nbins = N/2+1.
+ * Copied.  Builds the weights w[k] = 4 df / S_n[k] on the band (0 elsewhere,
+ * and 0 where S_n[k] <= 0 or is not finite).  Recomputes sigma^2 of a loaded
+ * bank.  Errors: MF_EINVAL (null, nbins != N/2+1). */
+mf_status mf_set_psd(mf_plan_t plan, const double* psd, int64_t nbins);
+
+/* Replace the template bank (Sec. II; Table I): n_tmpl one-sided templates
+ * h~_t[k], row t at htilde + t*ld elements, k = 0..N/2 (ld >= N/2+1).  dtype
+ * MF_F32 (scales must be NULL) or MF_F16 / MF_BF16 with host float32
+ * scales[n_tmpl] (h~ = scale_t * stored value).  on_device != 0: htilde is a
+ * device pointer, else host.  Copied into plan-owned device memory.  If the
+ * PSD is set, sigma_t^2 = sum_k w[k] |h~_t[k]|^2 is computed in float64 on the
+ * device (Eq. 2).  Errors: MF_EINVAL, MF_ENOMEM. */
+mf_status mf_load_bank(mf_plan_t plan, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld,
+                       const float* scales, int on_device);
+
+/* Reserve an empty bank of n_tmpl templates (zeros) to be filled in row
+ * blocks with mf_bank_set_rows; lets multi-GB banks be loaded piecewise. */
+mf_status mf_bank_reserve(mf_plan_t plan, mf_dtype dtype, int64_t n_tmpl);
+
+/* Copy rows [row0, row0+n_rows) of the bank (layout as mf_load_bank; scales
+ * host float32 [n_rows] or NULL for MF_F32) and compute their sigma^2. */
+mf_status mf_bank_set_rows(mf_plan_t plan, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
+                           const float* scales, int on_device);
+
+/* sigma_t^2 of templates 0..n-1 (float64, Eq. 2) into host out[n]; synchronises. */
+mf_status mf_get_sigmasq(mf_plan_t plan, double* out, int64_t n);
+
+/* A1 (Eq. 2 input): one-sided dt-normalised spectrum of real strain.
+ * strain: device float32 [n_det][ld_strain] (N samples used per detector);
+ * dtilde: device complex64 [n_det][ld_dtilde], ld_dtilde >= N/2+1, receives
+ * bins 0..N/2.  Asynchronous. */
+mf_status mf_strain_to_fd(mf_plan_t plan, const float* strain, int64_t ld_strain, void* dtilde, int64_t ld_dtilde);
+
+/* A2 (Sec. III, stage 1 at a reduced rate): the spectrum of the same data at
+ * this plan's (lower) rate is bins 0..N/2 of the higher-rate spectrum.
+ * dtilde_in: device complex64 [n_det][ld_in] with ld_in >= N/2+1 of this plan;
+ * dtilde_out: device complex64 [n_det][ld_out].  Asynchronous. */
+mf_status mf_decimate(mf_plan_t plan, const void* dtilde_in, int64_t ld_in, void* dtilde_out, int64_t ld_out);
+
+/* A4-A7 (Eq. 1-2, Sec. II, Sec. V.C): filter every detector of dtilde
+ * (device complex64 [n_det][ld_dtilde], one-sided spectra) against templates
+ * subset[0..n_subset-1] (device int32 template ids, ascending for ordered
+ * output); n_subset < 0 selects all templates (subset must then be NULL) and
+ * n_subset == 0 selects none (the trigger list becomes empty).  Computes
+ * z = IFFT(w s~ h~*), rho^2 = |z|^2 / sigma^2, threshold and window maxima
+ * entirely on the device; the SNR series never leaves on-chip memory.
+ * Asynchronous; results via mf_get_triggers.  Errors: MF_ESTATE (no PSD or
+ * bank), MF_EINVAL (bad template id range is not checked on the device:
+ * ids must be in [0, n_tmpl)). */
+mf_status mf_filter(mf_plan_t plan, const void* dtilde, int64_t ld_dtilde, const int32_t* subset, int64_t n_subset);
+
+/* Triggers of the last mf_filter, ordered by (det, position in the subset,
+ * sample), into host out[cap]; *n_found = total number found.  Synchronises.
+ * MF_EOVERFLOW if *n_found > cap or > max_triggers (the first
+ * min(cap, max_triggers) are returned). */
+mf_status mf_get_triggers(mf_plan_t plan, mf_trigger* out, int64_t cap, int64_t* n_found);
+
+/* Device view of the last filter's results: *trig = device mf_trigger array,
+ * *count = device int64 holding the number found (read after the stream
+ * completes).  Valid until the next mf_filter or mf_destroy. */
+mf_status mf_device_triggers(mf_plan_t plan, const mf_trigger** trig, const int64_t** count);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Counters of one plan.  launches: kernels this plan enqueued.  When profiling
+ * is on, CUDA events bracket the two filter kernels of each template batch on
+ * the plan's stream (up to 1024 batches between reads): pass1_* is the
+ * product + column-transform kernel, pass2_* the row-transform + SNR /
+ * threshold / window-max kernel; *_series = (template, detector) series they
+ * processed, *_ms = summed device time. */
+typedef struct {
+  int64_t launches;
+  int64_t pass1_launches, pass1_series;
+  double pass1_ms;
+  int64_t pass2_launches, pass2_series;
+  double pass2_ms;
+} mf_plan_stats;
+
+/* Turn event profiling of the filter kernels on (enable != 0) or off. */
+mf_status mf_profile(mf_plan_t plan, int enable);
+
+/* Read the counters into *out (synchronises the plan's stream); reset != 0
+ * zeroes them afterwards. */
+mf_status mf_get_stats(mf_plan_t plan, mf_plan_stats* out, int reset);
+
+/* ---- two-detector coincidence and follow-up (Sec. III) ---------------- */
+
+typedef struct {
+  int64_t shift_samples;   /* time-shift step, samples (> 0) */
+  int32_t n_shifts;        /* shifts k = 0..n_shifts (0 = zero lag only) */
+  int64_t window_samples;  /* coincidence window, samples (2*window < ring length) */
+  double rho_c_thr;        /* follow up a template when rho_c >= this */
+  double rho_c_store;      /* record coincidences with rho_c >= this */
+  int64_t max_coincs;      /* capacity of the coincidence record buffer */
+} mf_coinc_desc;
+
+typedef struct {
+  int32_t tmpl;
+  int32_t shift;      /* k */
+  int64_t sample0;    /* detector-0 trigger sample */
+  int64_t sample1;    /* detector-1 trigger sample (unshifted) */
+  float snr0, snr1;
+  float rho_c;        /* sqrt(snr0^2 + snr1^2) */
+  int32_t reserved;
+} mf_coinc;
+
+/* A8: on the last mf_filter of a 2-detector plan, find coincidences of
+ * detector-0 and detector-1 triggers of the same template: detector-1 times
+ * shifted by k*shift_samples (k = 0..n_shifts) on the ring of analysed
+ * samples [valid_begin, valid_end), circular distance <= window_samples.
+ * followed: device int32 [n_tmpl], zeroed here, set to 1 for templates with
+ * a coincidence of rho_c >= rho_c_thr.  Asynchronous. */
+mf_status mf_coincide(mf_plan_t plan, const mf_coinc_desc* desc, int32_t* followed);
+
+/* Coincidence records of the last mf_coincide, sorted by (tmpl, shift,
+ * sample0, sample1), into host out[cap].  Synchronises.  MF_EOVERFLOW as for
+ * triggers. */
+mf_status mf_get_coincs(mf_plan_t plan, mf_coinc* out, int64_t cap, int64_t* n_found);
+
+/* Neighbourhood map coarse -> fine (CSR: ptr int64 [n_coarse+1], idx int32
+ * [ptr[n_coarse]] fine template ids of this plan's bank), copied to the
+ * device; on_device selects the pointer kind. */
+mf_status mf_set_nbhd(mf_plan_t plan, const int64_t* ptr, const int32_t* idx, int64_t n_coarse, int on_device);
+
+/* A9: union of the neighbourhoods of coarse templates c with followed[c] != 0
+ * (device int32 [n_coarse]) as ascending fine ids into device subset
+ * [n_tmpl of this plan]; *n_subset (host) receives the count.  Synchronises. */
+mf_status mf_nbhd_union(mf_plan_t plan, const int32_t* followed, int32_t* subset, int64_t* n_subset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H_ */

@@ -1,0 +1,616 @@
+// C ABI of libmf (declared in include/mf.h): plan management, argument checks,
+// device memory ownership and the enqueueing of the kernels in
+// mf_kernels.cu / mf_glue.cu on the plan's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mf.h"
+#include "mf_internal.h"
+
+struct mf_plan_s {
+  mf_plan_desc d{};
+  cudaStream_t st = nullptr;
+  int n1 = 0, n2 = 0;
+  int64_t nb = 0, n_win = 0;
+  std::string err;
+  // PSD weights
+  std::vector<double> w_host;
+  double* w_dev = nullptr;
+  bool psd_set = false;
+  // bank
+  void* bank = nullptr;
+  mf_dtype bank_dtype = MF_F32;
+  int64_t n_tmpl = 0, ld_bank = 0;
+  float* scales_dev = nullptr;
+  double* sigmasq_dev = nullptr;
+  float* inv_sigma_dev = nullptr;
+  int32_t* sel_all = nullptr;
+  // filter work space
+  float2* q = nullptr;
+  int64_t ld_q = 0;
+  float2* scratch = nullptr;
+  int batch = 1;
+  unsigned long long* slots = nullptr;
+  int64_t slots_cap = 0;        // in slots
+  int32_t* sel_copy = nullptr;  // the selection of the last filter (device copy)
+  int64_t sel_cap = 0;
+  int64_t n_sel = 0;
+  bool filtered = false;
+  void* trig = nullptr;         // mf_trigger [max_triggers]
+  int64_t* count = nullptr;     // device int64
+  int64_t* bc = nullptr;        // compaction block offsets
+  int64_t bc_cap = 0;
+  // coincidence
+  void* coincs = nullptr;
+  int64_t coinc_cap = 0;
+  unsigned long long* n_coinc = nullptr;
+  float* maxrho = nullptr;
+  int64_t maxrho_cap = 0;
+  bool coinc_done = false;
+  // neighbourhood map
+  int64_t* nb_ptr = nullptr;
+  int32_t* nb_idx = nullptr;
+  int64_t n_coarse = 0;
+  int32_t* flags = nullptr;
+  int64_t flags_cap = 0;
+  int64_t* ubc = nullptr;
+  int64_t* ucount = nullptr;
+  // instrumentation
+  mf_plan_stats stats{};
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;      // pool, 3 per sampled batch
+  struct Sample {
+    int e0;
+    int64_t series;
+  };
+  std::vector<Sample> samples;      // batch samples awaiting read
+};
+
+namespace {
+constexpr int kProfBatches = 1024;
+
+// counts the kernels a block of code launches into p->stats.launches
+struct LaunchScope {
+  mf_plan_t p;
+  int64_t before;
+  explicit LaunchScope(mf_plan_t pp) : p(pp), before(mf::launch_count()) {}
+  ~LaunchScope() { p->stats.launches += mf::launch_count() - before; }
+};
+}  // namespace
+
+namespace {
+
+thread_local std::string g_err;
+
+mf_status fail(mf_plan_t p, mf_status s, const std::string& msg) {
+  if (p) p->err = msg; else g_err = msg;
+  return s;
+}
+
+mf_status cuda_fail(mf_plan_t p, cudaError_t e, const char* what) {
+  return fail(p, MF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+mf_status dalloc(mf_plan_t p, T** ptr, size_t bytes, const char* what) {
+  if (*ptr) {
+    cudaFree(*ptr);
+    *ptr = nullptr;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(p, MF_ENOMEM, std::string("cudaMalloc ") + what + " (" + std::to_string(bytes) + " bytes): " +
+                                  cudaGetErrorString(e));
+  }
+  return MF_OK;
+}
+
+template <class T>
+void dfree(T*& ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+size_t elem_bytes(mf_dtype t) { return t == MF_F32 ? 8 : 4; }
+
+int bank_type(mf_dtype t) { return t == MF_F32 ? mf::kBankF32 : (t == MF_F16 ? mf::kBankF16 : mf::kBankBF16); }
+
+// Analysis-band weights w[k] = 4 df / S_n[k] (Eq. 2): f_low <= k df < f_high,
+// 1 <= k <= N/2 - 1, S_n[k] positive and finite.
+void make_weights(const mf_plan_desc& d, const double* psd, std::vector<double>& w) {
+  const int64_t nb = d.n / 2 + 1;
+  const double df = d.fs / (double)d.n;
+  w.assign(nb, 0.0);
+  int64_t k_lo = (int64_t)std::ceil(d.f_low / df - 1e-9);
+  int64_t k_hi = (int64_t)std::ceil(d.f_high / df - 1e-9) - 1;
+  k_lo = std::max<int64_t>(k_lo, 1);
+  k_hi = std::min<int64_t>(k_hi, d.n / 2 - 1);
+  for (int64_t k = k_lo; k <= k_hi; ++k) {
+    const double s = psd[k];
+    if (std::isfinite(s) && s > 0.0) w[k] = 4.0 * df / s;
+  }
+}
+
+mf_status recompute_sigmasq(mf_plan_t p, int64_t row0, int64_t n_rows) {
+  if (!p->psd_set || !p->bank || n_rows <= 0) return MF_OK;
+  cudaError_t e = mf::launch_sigmasq(p->bank, bank_type(p->bank_dtype), p->ld_bank, p->scales_dev, row0, n_rows,
+                                     p->w_dev, p->nb, p->sigmasq_dev, p->inv_sigma_dev, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "sigma^2 kernel");
+  return MF_OK;
+}
+
+mf_status ensure_slots(mf_plan_t p, int64_t n_sel) {
+  const int64_t need = (int64_t)p->d.n_det * n_sel * p->n_win;
+  if (need > p->slots_cap) {
+    mf_status s = dalloc(p, &p->slots, (size_t)need * sizeof(unsigned long long), "window slots");
+    if (s != MF_OK) {
+      p->slots_cap = 0;
+      return s;
+    }
+    p->slots_cap = need;
+  }
+  const int64_t nblk = mf::compact_blocks(need);
+  if (nblk > p->bc_cap) {
+    mf_status s = dalloc(p, &p->bc, (size_t)std::max<int64_t>(nblk, 1) * sizeof(int64_t), "block offsets");
+    if (s != MF_OK) {
+      p->bc_cap = 0;
+      return s;
+    }
+    p->bc_cap = nblk;
+  }
+  if (n_sel > p->sel_cap) {
+    mf_status s = dalloc(p, &p->sel_copy, (size_t)std::max<int64_t>(n_sel, 1) * sizeof(int32_t), "selection");
+    if (s != MF_OK) {
+      p->sel_cap = 0;
+      return s;
+    }
+    p->sel_cap = n_sel;
+  }
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mf_last_error(mf_plan_t plan) { return plan ? plan->err.c_str() : g_err.c_str(); }
+
+mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
+  if (!out || !desc) return fail(nullptr, MF_EINVAL, "mf_plan: null argument");
+  const mf_plan_desc& d = *desc;
+  if (!is_pow2(d.n) || d.n < (1 << 12) || d.n > mf::kMaxN)
+    return fail(nullptr, MF_EINVAL, "mf_plan: n must be a power of two in [2^12, 2^20]");
+  if (!(d.fs > 0) || !std::isfinite(d.fs)) return fail(nullptr, MF_EINVAL, "mf_plan: fs must be positive");
+  if (d.n_det < 1 || d.n_det > 8) return fail(nullptr, MF_EINVAL, "mf_plan: n_det must be in 1..8");
+  if (!(d.f_low >= 0) || !(d.f_high > d.f_low)) return fail(nullptr, MF_EINVAL, "mf_plan: need 0 <= f_low < f_high");
+  if (d.dtype != MF_F32 && d.dtype != MF_F16 && d.dtype != MF_BF16) return fail(nullptr, MF_EINVAL, "mf_plan: dtype");
+  if (!(d.snr_thr > 0) || !std::isfinite(d.snr_thr)) return fail(nullptr, MF_EINVAL, "mf_plan: snr_thr must be > 0");
+  if (d.window < 1 || d.window > d.n) return fail(nullptr, MF_EINVAL, "mf_plan: window must be in [1, N]");
+  if (d.valid_begin < 0 || d.valid_end > d.n || d.valid_begin >= d.valid_end)
+    return fail(nullptr, MF_EINVAL, "mf_plan: need 0 <= valid_begin < valid_end <= N");
+  if (d.max_triggers < 1) return fail(nullptr, MF_EINVAL, "mf_plan: max_triggers must be >= 1");
+
+  mf_plan_t p = new (std::nothrow) mf_plan_s();
+  if (!p) return fail(nullptr, MF_ENOMEM, "mf_plan: host allocation");
+  p->d = d;
+  p->st = (cudaStream_t)d.cuda_stream;
+  int lg = 0;
+  while ((int64_t(1) << lg) < d.n) ++lg;
+  p->n1 = 1 << ((lg + 1) / 2);
+  p->n2 = 1 << (lg / 2);
+  p->nb = d.n / 2 + 1;
+  p->n_win = (d.n + d.window - 1) / d.window;
+  p->ld_q = (p->nb + 63) / 64 * 64;
+  // batch of templates per pass pair: keep the pass-1 -> pass-2 scratch within ~64 MB (L2 resident)
+  const int64_t per = (int64_t)d.n_det * d.n * (int64_t)sizeof(float2);
+  p->batch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t(64) << 20) / per, 4096));
+  mf_status s;
+  if ((s = dalloc(p, &p->w_dev, p->nb * sizeof(double), "weights")) != MF_OK ||
+      (s = dalloc(p, &p->q, (size_t)d.n_det * p->ld_q * sizeof(float2), "weighted data")) != MF_OK ||
+      (s = dalloc(p, &p->scratch, (size_t)p->batch * per, "scratch")) != MF_OK ||
+      (s = dalloc(p, &p->trig, (size_t)d.max_triggers * sizeof(mf_trigger), "triggers")) != MF_OK ||
+      (s = dalloc(p, &p->count, sizeof(int64_t), "count")) != MF_OK) {
+    g_err = p->err;
+    mf_destroy(p);
+    return s;
+  }
+  cudaMemsetAsync(p->count, 0, sizeof(int64_t), p->st);
+  *out = p;
+  return MF_OK;
+}
+
+void mf_destroy(mf_plan_t p) {
+  if (!p) return;
+  if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
+  dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev);
+  dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
+  dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
+  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount);
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  delete p;
+}
+
+mf_status mf_set_psd(mf_plan_t p, const double* psd, int64_t nbins) {
+  if (!p || !psd) return fail(p, MF_EINVAL, "mf_set_psd: null argument");
+  if (nbins != p->nb) return fail(p, MF_EINVAL, "mf_set_psd: nbins must be N/2+1");
+  make_weights(p->d, psd, p->w_host);
+  cudaError_t e = cudaMemcpyAsync(p->w_dev, p->w_host.data(), p->nb * sizeof(double), cudaMemcpyHostToDevice, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_psd copy");
+  e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_psd sync");
+  p->psd_set = true;
+  return recompute_sigmasq(p, 0, p->n_tmpl);
+}
+
+mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
+  if (!p) return fail(p, MF_EINVAL, "mf_bank_reserve: null plan");
+  if (dtype != MF_F32 && dtype != MF_F16 && dtype != MF_BF16) return fail(p, MF_EINVAL, "mf_bank_reserve: dtype");
+  if (n_tmpl < 1 || n_tmpl > 0x7fffffff) return fail(p, MF_EINVAL, "mf_bank_reserve: n_tmpl must be in [1, 2^31)");
+  cudaStreamSynchronize(p->st);
+  p->n_tmpl = 0;
+  p->bank_dtype = dtype;
+  p->ld_bank = (p->nb + 63) / 64 * 64;
+  const size_t bytes = (size_t)n_tmpl * p->ld_bank * elem_bytes(dtype);
+  mf_status s;
+  if ((s = dalloc(p, &p->bank, bytes, "bank")) != MF_OK ||
+      (s = dalloc(p, &p->sigmasq_dev, n_tmpl * sizeof(double), "sigma^2")) != MF_OK ||
+      (s = dalloc(p, &p->inv_sigma_dev, n_tmpl * sizeof(float), "1/sigma")) != MF_OK ||
+      (s = dalloc(p, &p->sel_all, n_tmpl * sizeof(int32_t), "all-template selection")) != MF_OK)
+    return s;
+  if (dtype != MF_F32) {
+    if ((s = dalloc(p, &p->scales_dev, n_tmpl * sizeof(float), "scales")) != MF_OK) return s;
+  } else {
+    dfree(p->scales_dev);
+  }
+  cudaError_t e = cudaMemsetAsync(p->bank, 0, bytes, p->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->sigmasq_dev, 0, n_tmpl * sizeof(double), p->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->inv_sigma_dev, 0, n_tmpl * sizeof(float), p->st);
+  std::vector<int32_t> ids(n_tmpl);
+  for (int64_t i = 0; i < n_tmpl; ++i) ids[i] = (int32_t)i;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->sel_all, ids.data(), n_tmpl * sizeof(int32_t), cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_reserve");
+  p->n_tmpl = n_tmpl;
+  return MF_OK;
+}
+
+mf_status mf_bank_set_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
+                           const float* scales, int on_device) {
+  if (!p || !htilde) return fail(p, MF_EINVAL, "mf_bank_set_rows: null argument");
+  if (!p->bank) return fail(p, MF_ESTATE, "mf_bank_set_rows: no bank reserved");
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > p->n_tmpl)
+    return fail(p, MF_EINVAL, "mf_bank_set_rows: rows out of range");
+  if (ld < p->nb) return fail(p, MF_EINVAL, "mf_bank_set_rows: ld must be >= N/2+1");
+  if ((p->bank_dtype == MF_F32) != (scales == nullptr))
+    return fail(p, MF_EINVAL, "mf_bank_set_rows: scales required for 16-bit banks and forbidden for MF_F32");
+  if (n_rows == 0) return MF_OK;
+  const size_t eb = elem_bytes(p->bank_dtype);
+  char* dst = (char*)p->bank + (size_t)row0 * p->ld_bank * eb;
+  cudaError_t e = cudaMemcpy2DAsync(dst, p->ld_bank * eb, htilde, ld * eb, p->nb * eb, n_rows,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess && scales)
+    e = cudaMemcpyAsync(p->scales_dev + row0, scales, n_rows * sizeof(float), cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_set_rows copy");
+  mf_status s = recompute_sigmasq(p, row0, n_rows);
+  if (s != MF_OK) return s;
+  e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_set_rows sigma^2");
+  return MF_OK;
+}
+
+mf_status mf_load_bank(mf_plan_t p, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld, const float* scales,
+                       int on_device) {
+  if (!p || !htilde) return fail(p, MF_EINVAL, "mf_load_bank: null argument");
+  mf_status s = mf_bank_reserve(p, dtype, n_tmpl);
+  if (s != MF_OK) return s;
+  return mf_bank_set_rows(p, 0, n_tmpl, htilde, ld, scales, on_device);
+}
+
+mf_status mf_get_sigmasq(mf_plan_t p, double* out, int64_t n) {
+  if (!p || !out) return fail(p, MF_EINVAL, "mf_get_sigmasq: null argument");
+  if (n < 0 || n > p->n_tmpl) return fail(p, MF_EINVAL, "mf_get_sigmasq: n out of range");
+  if (!p->psd_set) return fail(p, MF_ESTATE, "mf_get_sigmasq: PSD not set");
+  cudaError_t e = cudaMemcpyAsync(out, p->sigmasq_dev, n * sizeof(double), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_sigmasq");
+  return MF_OK;
+}
+
+mf_status mf_strain_to_fd(mf_plan_t p, const float* strain, int64_t ld_strain, void* dtilde, int64_t ld_dtilde) {
+  if (!p || !strain || !dtilde) return fail(p, MF_EINVAL, "mf_strain_to_fd: null argument");
+  if (ld_strain < p->d.n || ld_dtilde < p->nb) return fail(p, MF_EINVAL, "mf_strain_to_fd: leading dimension");
+  LaunchScope ls(p);
+  cudaError_t e = mf::launch_rfft(strain, ld_strain, p->d.n_det, p->d.n, p->n1, p->n2, 1.0 / p->d.fs, p->scratch,
+                                  (float2*)dtilde, ld_dtilde, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_strain_to_fd");
+  return MF_OK;
+}
+
+mf_status mf_decimate(mf_plan_t p, const void* in, int64_t ld_in, void* out, int64_t ld_out) {
+  if (!p || !in || !out) return fail(p, MF_EINVAL, "mf_decimate: null argument");
+  if (ld_in < p->nb || ld_out < p->nb) return fail(p, MF_EINVAL, "mf_decimate: leading dimension < N/2+1");
+  LaunchScope ls(p);
+  cudaError_t e = mf::launch_decimate((const float2*)in, ld_in, (float2*)out, ld_out, p->nb, p->d.n_det, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_decimate");
+  return MF_OK;
+}
+
+mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const int32_t* subset, int64_t n_subset) {
+  if (!p || !dtilde) return fail(p, MF_EINVAL, "mf_filter: null argument");
+  if (!p->psd_set) return fail(p, MF_ESTATE, "mf_filter: PSD not set");
+  if (!p->bank || p->n_tmpl == 0) return fail(p, MF_ESTATE, "mf_filter: no bank loaded");
+  if (ld_dtilde < p->nb) return fail(p, MF_EINVAL, "mf_filter: ld_dtilde < N/2+1");
+  if (n_subset < 0 && subset) return fail(p, MF_EINVAL, "mf_filter: n_subset < 0 (all templates) needs subset NULL");
+  if (n_subset > 0 && !subset) return fail(p, MF_EINVAL, "mf_filter: subset is NULL");
+  const int64_t n_sel = n_subset < 0 ? p->n_tmpl : n_subset;
+  mf_status s = ensure_slots(p, std::max<int64_t>(n_sel, 1));
+  if (s != MF_OK) return s;
+  cudaError_t e = cudaSuccess;
+  if (n_sel > 0)
+    e = cudaMemcpyAsync(p->sel_copy, n_subset < 0 ? p->sel_all : subset, n_sel * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                        p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter selection copy");
+  const int64_t n_slots = (int64_t)p->d.n_det * n_sel * p->n_win;
+  const int64_t launches_before = mf::launch_count();
+  e = mf::launch_prep((const float2*)dtilde, ld_dtilde, p->w_dev, p->nb, p->d.n_det, p->q, p->ld_q, p->slots, n_slots,
+                      p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter prep");
+  mf::FilterArgs a{};
+  a.n = p->d.n;
+  a.n1 = p->n1;
+  a.n2 = p->n2;
+  a.n_det = p->d.n_det;
+  a.nb = p->nb;
+  a.bank = p->bank;
+  a.bank_type = bank_type(p->bank_dtype);
+  a.ld_bank = p->ld_bank;
+  a.scales = p->scales_dev;
+  a.q = p->q;
+  a.ld_q = p->ld_q;
+  a.sel = p->sel_copy;
+  a.inv_sigma = p->inv_sigma_dev;
+  a.scratch = p->scratch;
+  const double thr = p->d.snr_thr;
+  a.thr2 = (float)(thr * thr);
+  a.window = p->d.window;
+  a.valid_begin = p->d.valid_begin;
+  a.valid_end = p->d.valid_end;
+  a.n_win = p->n_win;
+  a.n_sel_total = n_sel;
+  a.slots = p->slots;
+  LaunchScope ls(p);
+  ls.before = launches_before;
+  for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
+    a.pos0 = pos0;
+    a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
+    const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
+    const int e0 = prof ? (int)p->samples.size() * 3 : 0;
+    if (prof) cudaEventRecord(p->ev[e0], p->st);
+    e = mf::launch_filter_pass1(a, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 1");
+    if (prof) cudaEventRecord(p->ev[e0 + 1], p->st);
+    e = mf::launch_filter_pass2(a, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 2");
+    if (prof) {
+      cudaEventRecord(p->ev[e0 + 2], p->st);
+      p->samples.push_back({e0, (int64_t)a.count * p->d.n_det});
+    }
+  }
+  e = mf::launch_compact(p->slots, p->d.n_det, n_sel, p->n_win, p->d.window, p->sel_copy, p->trig, p->d.max_triggers,
+                         p->count, p->bc, p->bc_cap, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter compaction");
+  p->n_sel = n_sel;
+  p->filtered = true;
+  p->coinc_done = false;
+  return MF_OK;
+}
+
+mf_status mf_profile(mf_plan_t p, int enable) {
+  if (!p) return fail(p, MF_EINVAL, "mf_profile: null plan");
+  if (enable && p->ev.empty()) {
+    p->ev.resize(3 * kProfBatches);
+    for (auto& e : p->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return cuda_fail(p, r, "mf_profile event");
+    }
+  }
+  p->prof = enable != 0;
+  return MF_OK;
+}
+
+mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
+  if (!p || !out) return fail(p, MF_EINVAL, "mf_get_stats: null argument");
+  cudaError_t e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_stats sync");
+  for (const auto& sm : p->samples) {
+    float t1 = 0, t2 = 0;
+    e = cudaEventElapsedTime(&t1, p->ev[sm.e0], p->ev[sm.e0 + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, p->ev[sm.e0 + 1], p->ev[sm.e0 + 2]);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_stats elapsed");
+    p->stats.pass1_launches += 1;
+    p->stats.pass1_series += sm.series;
+    p->stats.pass1_ms += t1;
+    p->stats.pass2_launches += 1;
+    p->stats.pass2_series += sm.series;
+    p->stats.pass2_ms += t2;
+  }
+  p->samples.clear();
+  *out = p->stats;
+  if (reset) p->stats = mf_plan_stats{};
+  return MF_OK;
+}
+
+mf_status mf_get_triggers(mf_plan_t p, mf_trigger* out, int64_t cap, int64_t* n_found) {
+  if (!p || !n_found || (cap > 0 && !out)) return fail(p, MF_EINVAL, "mf_get_triggers: null argument");
+  if (!p->filtered) return fail(p, MF_ESTATE, "mf_get_triggers: no filter run");
+  int64_t n = 0;
+  cudaError_t e = cudaMemcpyAsync(&n, p->count, sizeof(int64_t), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_triggers count");
+  *n_found = n;
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(n, cap), p->d.max_triggers);
+  if (m > 0) {
+    e = cudaMemcpyAsync(out, p->trig, m * sizeof(mf_trigger), cudaMemcpyDeviceToHost, p->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_triggers copy");
+  }
+  if (n > cap || n > p->d.max_triggers)
+    return fail(p, MF_EOVERFLOW, "mf_get_triggers: " + std::to_string(n) + " triggers exceed the buffer");
+  return MF_OK;
+}
+
+mf_status mf_device_triggers(mf_plan_t p, const mf_trigger** trig, const int64_t** count) {
+  if (!p || !trig || !count) return fail(p, MF_EINVAL, "mf_device_triggers: null argument");
+  if (!p->filtered) return fail(p, MF_ESTATE, "mf_device_triggers: no filter run");
+  *trig = (const mf_trigger*)p->trig;
+  *count = p->count;
+  return MF_OK;
+}
+
+mf_status mf_coincide(mf_plan_t p, const mf_coinc_desc* c, int32_t* followed) {
+  if (!p || !c || !followed) return fail(p, MF_EINVAL, "mf_coincide: null argument");
+  if (p->d.n_det != 2) return fail(p, MF_EINVAL, "mf_coincide: needs a 2-detector plan");
+  if (!p->filtered) return fail(p, MF_ESTATE, "mf_coincide: no filter run");
+  const int64_t R = p->d.valid_end - p->d.valid_begin;
+  if (c->shift_samples <= 0 || c->n_shifts < 0 || c->window_samples < 0 || 2 * c->window_samples >= R ||
+      c->max_coincs < 1 || !(c->rho_c_thr > 0) || !(c->rho_c_store > 0))
+    return fail(p, MF_EINVAL, "mf_coincide: bad coincidence description");
+  mf_status s;
+  if (c->max_coincs > p->coinc_cap) {
+    if ((s = dalloc(p, &p->coincs, (size_t)c->max_coincs * sizeof(mf_coinc), "coincidences")) != MF_OK) {
+      p->coinc_cap = 0;
+      return s;
+    }
+    p->coinc_cap = c->max_coincs;
+  }
+  if (!p->n_coinc && (s = dalloc(p, &p->n_coinc, sizeof(unsigned long long), "coincidence count")) != MF_OK) return s;
+  if (p->n_sel > p->maxrho_cap) {
+    if ((s = dalloc(p, &p->maxrho, (size_t)p->n_sel * sizeof(float), "max rho^2")) != MF_OK) {
+      p->maxrho_cap = 0;
+      return s;
+    }
+    p->maxrho_cap = p->n_sel;
+  }
+  cudaError_t e = cudaMemsetAsync(followed, 0, p->n_tmpl * sizeof(int32_t), p->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->n_coinc, 0, sizeof(unsigned long long), p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_coincide reset");
+  mf::CoincArgs a{};
+  a.slots = p->slots;
+  a.sel = p->sel_copy;
+  a.n_sel = p->n_sel;
+  a.n_win = p->n_win;
+  a.window = p->d.window;
+  a.ring_begin = p->d.valid_begin;
+  a.ring_end = p->d.valid_end;
+  a.shift = c->shift_samples;
+  a.n_shifts = c->n_shifts;
+  a.coinc_window = c->window_samples;
+  a.rho_c_thr2 = (float)(c->rho_c_thr * c->rho_c_thr);
+  a.rho_c_store2 = (float)(c->rho_c_store * c->rho_c_store);
+  a.followed = followed;
+  a.coincs = p->coincs;
+  a.coinc_cap = p->coinc_cap;
+  a.n_coinc = p->n_coinc;
+  LaunchScope ls(p);
+  e = mf::launch_coinc(a, p->maxrho, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_coincide kernels");
+  p->coinc_done = true;
+  return MF_OK;
+}
+
+mf_status mf_get_coincs(mf_plan_t p, mf_coinc* out, int64_t cap, int64_t* n_found) {
+  if (!p || !n_found || (cap > 0 && !out)) return fail(p, MF_EINVAL, "mf_get_coincs: null argument");
+  if (!p->coinc_done) return fail(p, MF_ESTATE, "mf_get_coincs: no coincidence run");
+  unsigned long long n = 0;
+  cudaError_t e = cudaMemcpyAsync(&n, p->n_coinc, sizeof(n), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_coincs count");
+  *n_found = (int64_t)n;
+  const int64_t have = std::min<int64_t>((int64_t)n, p->coinc_cap);
+  std::vector<mf_coinc> all(have);
+  if (have > 0) {
+    e = cudaMemcpyAsync(all.data(), p->coincs, have * sizeof(mf_coinc), cudaMemcpyDeviceToHost, p->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_coincs copy");
+  }
+  std::sort(all.begin(), all.end(), [](const mf_coinc& a, const mf_coinc& b) {
+    if (a.tmpl != b.tmpl) return a.tmpl < b.tmpl;
+    if (a.shift != b.shift) return a.shift < b.shift;
+    if (a.sample0 != b.sample0) return a.sample0 < b.sample0;
+    return a.sample1 < b.sample1;
+  });
+  const int64_t m = std::min<int64_t>(have, cap);
+  if (m > 0) std::memcpy(out, all.data(), m * sizeof(mf_coinc));
+  if ((int64_t)n > cap || (int64_t)n > p->coinc_cap)
+    return fail(p, MF_EOVERFLOW, "mf_get_coincs: " + std::to_string(n) + " coincidences exceed the buffer");
+  return MF_OK;
+}
+
+mf_status mf_set_nbhd(mf_plan_t p, const int64_t* ptr, const int32_t* idx, int64_t n_coarse, int on_device) {
+  if (!p || !ptr || (n_coarse > 0 && !idx)) return fail(p, MF_EINVAL, "mf_set_nbhd: null argument");
+  if (n_coarse < 0) return fail(p, MF_EINVAL, "mf_set_nbhd: negative n_coarse");
+  int64_t nnz = 0;
+  cudaError_t e = cudaSuccess;
+  if (on_device) {
+    e = cudaMemcpy(&nnz, ptr + n_coarse, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_nbhd read nnz");
+  } else {
+    nnz = ptr[n_coarse];
+    if (ptr[0] != 0) return fail(p, MF_EINVAL, "mf_set_nbhd: ptr[0] must be 0");
+    for (int64_t c = 0; c < n_coarse; ++c)
+      if (ptr[c + 1] < ptr[c]) return fail(p, MF_EINVAL, "mf_set_nbhd: ptr must be non-decreasing");
+    for (int64_t i = 0; i < nnz; ++i)
+      if (idx[i] < 0 || idx[i] >= p->n_tmpl) return fail(p, MF_EINVAL, "mf_set_nbhd: fine id out of range");
+  }
+  if (nnz < 0) return fail(p, MF_EINVAL, "mf_set_nbhd: negative nnz");
+  mf_status s;
+  if ((s = dalloc(p, &p->nb_ptr, (n_coarse + 1) * sizeof(int64_t), "nbhd ptr")) != MF_OK ||
+      (s = dalloc(p, &p->nb_idx, std::max<int64_t>(nnz, 1) * sizeof(int32_t), "nbhd idx")) != MF_OK)
+    return s;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  e = cudaMemcpy(p->nb_ptr, ptr, (n_coarse + 1) * sizeof(int64_t), kind);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpy(p->nb_idx, idx, nnz * sizeof(int32_t), kind);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_nbhd copy");
+  p->n_coarse = n_coarse;
+  return MF_OK;
+}
+
+mf_status mf_nbhd_union(mf_plan_t p, const int32_t* followed, int32_t* subset, int64_t* n_subset) {
+  if (!p || !followed || !subset || !n_subset) return fail(p, MF_EINVAL, "mf_nbhd_union: null argument");
+  if (!p->nb_ptr) return fail(p, MF_ESTATE, "mf_nbhd_union: no neighbourhood map");
+  if (p->n_tmpl < 1) return fail(p, MF_ESTATE, "mf_nbhd_union: no bank");
+  mf_status s;
+  if (p->flags_cap < p->n_tmpl) {
+    p->flags_cap = 0;
+    if ((s = dalloc(p, &p->flags, p->n_tmpl * sizeof(int32_t), "union flags")) != MF_OK ||
+        (s = dalloc(p, &p->ubc, ((p->n_tmpl + 1023) / 1024 + 1) * sizeof(int64_t), "union blocks")) != MF_OK ||
+        (s = dalloc(p, &p->ucount, sizeof(int64_t), "union count")) != MF_OK)
+      return s;
+    p->flags_cap = p->n_tmpl;
+  }
+  LaunchScope ls(p);
+  cudaError_t e = mf::launch_union(p->nb_ptr, p->nb_idx, p->n_coarse, followed, p->flags, p->n_tmpl, subset,
+                                   p->ucount, p->ubc, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_nbhd_union kernels");
+  int64_t n = 0;
+  e = cudaMemcpyAsync(&n, p->ucount, sizeof(int64_t), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_nbhd_union count");
+  *n_subset = n;
+  return MF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal launcher interface between the C-ABI layer (mf_api.cu) and the
+// kernels (mf_kernels.cu, mf_glue.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mf {
+
+// Packed per-window maximum: [63:32] float bits of rho^2 (>= 0, so integer
+// order = float order), [31:11] (2^21 - 1 - sample) so that ties go to the
+// lowest sample, [10:0] phase of z quantised to 2 pi / 2048.
+constexpr int kSampleBits = 21;
+constexpr int kPhaseBits = 11;
+constexpr int64_t kMaxN = int64_t(1) << 20;
+
+enum BankType { kBankF32 = 0, kBankF16 = 1, kBankBF16 = 2 };
+
+struct FilterArgs {
+  // geometry
+  int64_t n;          // FFT length N
+  int n1, n2;         // N = n1 * n2 (pass-1 column length, pass-2 row length)
+  int n_det;
+  int64_t nb;         // N/2 + 1
+  // inputs
+  const void* bank;   // [n_tmpl][ld_bank] complex (f32 pairs or 16-bit pairs)
+  int bank_type;
+  int64_t ld_bank;
+  const float* scales;      // per template (16-bit banks), may be null
+  const float2* q;          // weighted data [n_det][ld_q]
+  int64_t ld_q;
+  const int32_t* sel;       // selection: position -> template id (device)
+  const float* inv_sigma;   // per template id: 1 / sigma
+  // this batch: selection positions [pos0, pos0 + count)
+  int64_t pos0;
+  int count;
+  float2* scratch;          // [count * n_det][n1][n2]
+  // epilogue
+  float thr2;
+  int64_t window;
+  int64_t valid_begin, valid_end;
+  int64_t n_win;
+  int64_t n_sel_total;      // slots are [n_det][n_sel_total][n_win]
+  unsigned long long* slots;
+};
+
+// Number of kernels launched by this library (all plans, all threads).
+int64_t launch_count();
+void add_launches(int64_t n);
+
+cudaError_t launch_prep(const float2* dtilde, int64_t ld_d, const double* w, int64_t nb, int n_det,
+                        float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots,
+                        cudaStream_t st);
+cudaError_t launch_filter_batch(const FilterArgs& a, cudaStream_t st);
+// the two halves of launch_filter_batch, for per-kernel timing
+cudaError_t launch_filter_pass1(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_filter_pass2(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_sigmasq(const void* bank, int bank_type, int64_t ld_bank, const float* scales,
+                           int64_t row0, int64_t n_rows, const double* w, int64_t nb,
+                           double* sigmasq, float* inv_sigma, cudaStream_t st);
+// compaction of window maxima into mf_trigger records (layout of the public struct)
+cudaError_t launch_compact(const unsigned long long* slots, int n_det, int64_t n_sel, int64_t n_win,
+                           int64_t window, const int32_t* sel, void* trig_out, int64_t trig_cap,
+                           int64_t* count, int64_t* block_counts, int64_t n_blocks_cap, cudaStream_t st);
+int64_t compact_blocks(int64_t n_slots);
+// time series -> one-sided dt-normalised spectrum (A1)
+cudaError_t launch_rfft(const float* strain, int64_t ld_s, int n_det, int64_t n, int n1, int n2, double dt,
+                        float2* scratch, float2* dtilde, int64_t ld_d, cudaStream_t st);
+// keep bins 0..nb_out-1 (A2)
+cudaError_t launch_decimate(const float2* in, int64_t ld_in, float2* out, int64_t ld_out, int64_t nb_out,
+                            int n_det, cudaStream_t st);
+
+struct CoincArgs {
+  const unsigned long long* slots;  // stage-1 window maxima [2][n_sel][n_win]
+  const int32_t* sel;
+  int64_t n_sel, n_win, window;
+  int64_t ring_begin, ring_end;
+  int64_t shift;                    // samples per time shift
+  int n_shifts;                     // k = 0..n_shifts
+  int64_t coinc_window;             // samples
+  float rho_c_thr2;                 // follow-up threshold on rho_c^2
+  float rho_c_store2;               // store coincidences with rho_c^2 >= this
+  int32_t* followed;                // [n_tmpl] flags (written 1)
+  void* coincs;                     // mf_coinc records
+  int64_t coinc_cap;
+  unsigned long long* n_coinc;      // counter
+  const float* max_rho2_det1;       // per selection position, max rho^2 of detector 1 (prefilter)
+};
+cudaError_t launch_coinc(const CoincArgs& a, float* max_rho2_det1, cudaStream_t st);
+cudaError_t launch_union(const int64_t* ptr, const int32_t* idx, int64_t n_coarse, const int32_t* followed,
+                         int32_t* flags, int64_t n_fine, int32_t* subset, int64_t* n_subset,
+                         int64_t* block_counts, cudaStream_t st);
+
+}  // namespace mf

@@ -1,0 +1,625 @@
+// Matched-filter kernels for sm_103a: weighted data, FP64 template norms,
+// the fused product + inverse FFT + SNR/threshold/window-max filter, and the
+// compaction of window maxima into triggers.
+//
+// The filter computes, for template h and detector data s (Eq. 1-2, Sec. V.C),
+//   z[n] = sum_k w[k] s~[k] h~*[k] exp(+2 pi i n k / N),  w = 4 df / S_n on the band,
+//   rho^2[n] = |z[n]|^2 / sigma^2,  sigma^2 = sum_k w |h~[k]|^2,
+// keeps n with rho^2 >= rho_thr^2 (Sec. II, inclusive) and reduces them to one
+// maximum per window of W samples.  The N-point transform is a four-step
+// N = N1 * N2: pass 1 forms the product while loading and does N1-point column
+// transforms (k = k1 N2 + k2, the upper half k1 >= N1/2 is the empty negative
+// frequency half), multiplies by exp(+2 pi i j1 k2 / N) and writes an
+// L2-resident scratch; pass 2 does N2-point row transforms and evaluates
+// rho^2 of z[j1 + N1 j2] in registers, so the SNR series never reaches memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mf_fft.cuh"
+#include "mf_internal.h"
+
+namespace mf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Shared-memory stride of one column/row: >= pad and congruent to L (mod 16),
+// where L = consecutive-thread lanes a group contributes to a half-warp, so
+// 64-bit shared accesses of a half-warp hit 16 distinct bank pairs.
+constexpr int stride_for(int pad, int lanes) {
+  int L = lanes >= 16 ? 0 : lanes;
+  int s = pad;
+  if (L == 0) return s;
+  while (s % 16 != L) ++s;
+  return s;
+}
+
+template <int N1>
+struct P1Geo {
+  using G = SubFft<N1>;
+  static constexpr int C = kThreads / G::T;  // columns per CTA
+  static constexpr int L = C >= 16 ? 1 : 16 / C;
+  static constexpr int S = stride_for(G::PAD, L);
+  static constexpr int SMEM = C * S * (int)sizeof(float2);
+};
+
+template <int N2>
+struct P2Geo {
+  using G = SubFft<N2>;
+  static constexpr int RW = kThreads / G::T;  // rows per CTA
+  static constexpr int L = G::T >= 16 ? 16 : G::T;
+  static constexpr int S = stride_for(G::PAD, L);
+  static constexpr int SMEM = RW * S * (int)sizeof(float2);
+};
+
+// u[r] *= b^r, r = 1..R-1 (running product)
+template <int R>
+__device__ __forceinline__ void twiddle_run(float2 (&u)[R], float2 b) {
+  float2 w = b;
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    u[r] = cmul(u[r], w);
+    if (r + 1 < R) w = cmul(w, b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// loaders (pass 1 input) and epilogues (pass 2 output)
+// ---------------------------------------------------------------------------
+
+template <int BT>
+struct BankElem;
+template <>
+struct BankElem<kBankF32> {
+  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
+    return __ldg(reinterpret_cast<const float2*>(p) + i);
+  }
+};
+template <>
+struct BankElem<kBankF16> {
+  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
+    __half2 h = __ldg(reinterpret_cast<const __half2*>(p) + i);
+    return __half22float2(h);
+  }
+};
+template <>
+struct BankElem<kBankBF16> {
+  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
+    __nv_bfloat162 h = __ldg(reinterpret_cast<const __nv_bfloat162*>(p) + i);
+    return __bfloat1622float2(h);
+  }
+};
+
+// x[k] = q_d[k] conj(h_t[k]); series s = b * n_det + d, template t = sel[pos0 + b]
+template <int BT>
+struct FilterLoad {
+  const void* bank;
+  int64_t ld_bank;
+  const float2* q;
+  int64_t ld_q;
+  const int32_t* sel;
+  int64_t pos0;
+  int n_det;
+  int64_t nb;
+  struct Ser {
+    const float2* qd;
+    int64_t hoff;
+  };
+  __device__ __forceinline__ Ser series(int s) const {
+    const int d = s % n_det;
+    const int64_t t = sel[pos0 + s / n_det];
+    return Ser{q + (int64_t)d * ld_q, t * ld_bank};
+  }
+  __device__ __forceinline__ float2 value(const Ser& se, int64_t k) const {
+    if (k >= nb) return make_float2(0.f, 0.f);
+    float2 qv = __ldg(se.qd + k);
+    float2 hv = BankElem<BT>::get(bank, se.hoff + k);
+    return cmulc(qv, hv);
+  }
+};
+
+// real strain -> complex input (forward transform via conjugation at the end)
+struct RealLoad {
+  const float* x;
+  int64_t ld;
+  struct Ser {
+    const float* xd;
+  };
+  __device__ __forceinline__ Ser series(int s) const { return Ser{x + (int64_t)s * ld}; }
+  __device__ __forceinline__ float2 value(const Ser& se, int64_t k) const {
+    return make_float2(__ldg(se.xd + k), 0.f);
+  }
+};
+
+struct FilterEpi {
+  const int32_t* sel;
+  const float* inv_sigma;
+  int64_t pos0;
+  int n_det;
+  float thr2;
+  int64_t window, vb, ve, n_win, n_sel_total;
+  unsigned long long* slots;
+  struct Ser {
+    float is;
+    unsigned long long* slot;
+  };
+  __device__ __forceinline__ Ser series(int s) const {
+    const int d = s % n_det;
+    const int64_t pos = pos0 + s / n_det;
+    return Ser{__ldg(inv_sigma + sel[pos]), slots + ((int64_t)d * n_sel_total + pos) * n_win};
+  }
+  __device__ __forceinline__ void operator()(const Ser& se, int64_t n, float2 z) const {
+    const float a = z.x * se.is, b = z.y * se.is;
+    const float r2 = fmaf(a, a, b * b);
+    if (r2 >= thr2) {
+      if (n < vb || n >= ve) return;
+      const float ph = atan2f(b, a);
+      const uint32_t code = (uint32_t)__float2int_rn(fmaf(ph, 0.15915494309189535f, 0.5f) * 2048.0f) & 2047u;
+      const unsigned long long key = ((unsigned long long)__float_as_uint(r2) << 32) |
+                                     ((unsigned long long)(((1u << kSampleBits) - 1u) - (uint32_t)n) << kPhaseBits) |
+                                     code;
+      atomicMax(se.slot + n / window, key);
+    }
+  }
+};
+
+// forward one-sided spectrum: dtilde[n] = dt * conj(z[n]) for n <= N/2
+struct SpectrumEpi {
+  float2* out;
+  int64_t ld;
+  int64_t nb;
+  float dt;
+  struct Ser {
+    float2* o;
+  };
+  __device__ __forceinline__ Ser series(int s) const { return Ser{out + (int64_t)s * ld}; }
+  __device__ __forceinline__ void operator()(const Ser& se, int64_t n, float2 z) const {
+    if (n < nb) se.o[n] = make_float2(z.x * dt, -z.y * dt);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// pass 1: column transforms (length N1) of series s, product fused into the load
+// ---------------------------------------------------------------------------
+
+template <int N1, int N2, bool HALF, class Load>
+__global__ void __launch_bounds__(kThreads, 2) k_pass1(Load ld, float2* __restrict__ scratch, int n_series) {
+  using G = SubFft<N1>;
+  using P = P1Geo<N1>;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C;
+  constexpr int NCB = N2 / C;
+  constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
+  extern __shared__ float2 sm[];
+  const int c = threadIdx.x % C;
+  const int t = threadIdx.x / C;
+  float2* col = sm + c * P::S;
+  const int n_items = n_series * NCB;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int s = item / NCB;
+    const int k2 = (item % NCB) * C + c;
+    const auto se = ld.series(s);
+    float2 v[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      if (HALF && r >= RA / 2) {
+        v[r] = make_float2(0.f, 0.f);
+      } else {
+        const int k1 = t + r * RB;
+        v[r] = ld.value(se, (int64_t)k1 * N2 + k2);
+      }
+    }
+    dft<RA, HALF>(v);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RA; ++a) col[G::pidx(t * RA + a)] = v[a];
+    __syncthreads();
+    float2* out = scratch + (int64_t)s * N;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = t + T * i;
+      float2 u[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) u[r] = col[G::pidx(j + r * RA)];
+      twiddle_run<RB>(u, unit_root((uint32_t)j, (uint32_t)N1));
+      dft<RB>(u);
+      // four-step twiddle exp(+2 pi i j1 k2 / N), j1 = j + a RA
+      float2 w = unit_root(((uint32_t)j * (uint32_t)k2) & (N - 1), N);
+      const float2 st = unit_root(((uint32_t)RA * (uint32_t)k2) & (N - 1), N);
+#pragma unroll
+      for (int a = 0; a < RB; ++a) {
+        out[(int64_t)(j + a * RA) * N2 + k2] = cmul(u[a], w);
+        if (a + 1 < RB) w = cmul(w, st);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: row transforms (length N2) + epilogue on z[j1 + N1 j2]
+// ---------------------------------------------------------------------------
+
+template <int N1, int N2, class Epi>
+__global__ void __launch_bounds__(kThreads, 2) k_pass2(const float2* __restrict__ scratch, Epi epi, int n_series) {
+  using G = SubFft<N2>;
+  using P = P2Geo<N2>;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW;
+  constexpr int NRB = N1 / RW;
+  constexpr int64_t N = (int64_t)N1 * N2;
+  extern __shared__ float2 sm[];
+  const int t = threadIdx.x % T;
+  const int row = threadIdx.x / T;
+  float2* rs = sm + row * P::S;
+  const int n_items = n_series * NRB;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int s = item / NRB;
+    const int j1 = (item % NRB) * RW + row;
+    const float2* in = scratch + (int64_t)s * N + (int64_t)j1 * N2;
+    float2 v[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) v[r] = in[t + r * RB];
+    dft<RA>(v);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RA; ++a) rs[G::pidx(t * RA + a)] = v[a];
+    __syncthreads();
+    const auto se = epi.series(s);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = t + T * i;
+      float2 u[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) u[r] = rs[G::pidx(j + r * RA)];
+      twiddle_run<RB>(u, unit_root((uint32_t)j, (uint32_t)N2));
+      dft<RB>(u);
+#pragma unroll
+      for (int a = 0; a < RB; ++a) epi(se, (int64_t)j1 + (int64_t)N1 * (j + a * RA), u[a]);
+    }
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <class K>
+cudaError_t set_smem(K kern, int bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int grid_for(int n_items, int per_sm) {
+  int g = num_sms() * per_sm;
+  return n_items < g ? n_items : g;
+}
+
+int64_t g_launches = 0;
+
+template <int N1, int N2, int BT>
+cudaError_t run_pass1(const FilterArgs& a, cudaStream_t st) {
+  const int n_series = a.count * a.n_det;
+  FilterLoad<BT> ld{a.bank, a.ld_bank, a.q, a.ld_q, a.sel, a.pos0, a.n_det, a.nb};
+  auto k1 = k_pass1<N1, N2, true, FilterLoad<BT>>;
+  cudaError_t e = set_smem(k1, P1Geo<N1>::SMEM);
+  if (e != cudaSuccess) return e;
+  const int items1 = n_series * (N2 / P1Geo<N1>::C);
+  k1<<<grid_for(items1, 2), kThreads, P1Geo<N1>::SMEM, st>>>(ld, a.scratch, n_series);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <int N1, int N2>
+cudaError_t run_pass2(const FilterArgs& a, cudaStream_t st) {
+  const int n_series = a.count * a.n_det;
+  FilterEpi ep{a.sel, a.inv_sigma, a.pos0, a.n_det, a.thr2, a.window, a.valid_begin, a.valid_end,
+               a.n_win, a.n_sel_total, a.slots};
+  auto k2 = k_pass2<N1, N2, FilterEpi>;
+  cudaError_t e = set_smem(k2, P2Geo<N2>::SMEM);
+  if (e != cudaSuccess) return e;
+  const int items2 = n_series * (N1 / P2Geo<N2>::RW);
+  k2<<<grid_for(items2, 2), kThreads, P2Geo<N2>::SMEM, st>>>(a.scratch, ep, n_series);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <int N1, int N2>
+cudaError_t run_pass1_bt(const FilterArgs& a, cudaStream_t st) {
+  switch (a.bank_type) {
+    case kBankF32: return run_pass1<N1, N2, kBankF32>(a, st);
+    case kBankF16: return run_pass1<N1, N2, kBankF16>(a, st);
+    case kBankBF16: return run_pass1<N1, N2, kBankBF16>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// dispatch on N to the instantiation with N = N1 * N2 (N1 >= N2)
+#define MF_DISPATCH_N(n, FN, ARGS)                   \
+  switch (n) {                                       \
+    case 1 << 12: return FN<64, 64> ARGS;            \
+    case 1 << 13: return FN<128, 64> ARGS;           \
+    case 1 << 14: return FN<128, 128> ARGS;          \
+    case 1 << 15: return FN<256, 128> ARGS;          \
+    case 1 << 16: return FN<256, 256> ARGS;          \
+    case 1 << 17: return FN<512, 256> ARGS;          \
+    case 1 << 18: return FN<512, 512> ARGS;          \
+    case 1 << 19: return FN<1024, 512> ARGS;         \
+    case 1 << 20: return FN<1024, 1024> ARGS;        \
+  }                                                  \
+  return cudaErrorInvalidValue;
+
+template <int N1, int N2>
+cudaError_t run_rfft(const float* x, int64_t ld_s, int n_det, double dt, float2* scratch, float2* out,
+                     int64_t ld_d, cudaStream_t st) {
+  RealLoad ld{x, ld_s};
+  auto k1 = k_pass1<N1, N2, false, RealLoad>;
+  cudaError_t e = set_smem(k1, P1Geo<N1>::SMEM);
+  if (e != cudaSuccess) return e;
+  k1<<<grid_for(n_det * (N2 / P1Geo<N1>::C), 2), kThreads, P1Geo<N1>::SMEM, st>>>(ld, scratch, n_det);
+  SpectrumEpi ep{out, ld_d, (int64_t)N1 * N2 / 2 + 1, (float)dt};
+  auto k2 = k_pass2<N1, N2, SpectrumEpi>;
+  e = set_smem(k2, P2Geo<N2>::SMEM);
+  if (e != cudaSuccess) return e;
+  k2<<<grid_for(n_det * (N1 / P2Geo<N2>::RW), 2), kThreads, P2Geo<N2>::SMEM, st>>>(scratch, ep, n_det);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_prep(const float2* __restrict__ d, int64_t ld_d, const double* __restrict__ w, int64_t nb,
+                       int n_det, float2* __restrict__ q, int64_t ld_q) {
+  const int64_t total = nb * n_det;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int det = (int)(i / nb);
+    const int64_t k = i - (int64_t)det * nb;
+    const double wk = w[k];
+    const float2 s = d[(int64_t)det * ld_d + k];
+    q[(int64_t)det * ld_q + k] = make_float2((float)(wk * (double)s.x), (float)(wk * (double)s.y));
+  }
+}
+
+__global__ void k_zero_u64(unsigned long long* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0ull;
+}
+
+template <int BT>
+__global__ void k_sigmasq(const void* bank, int64_t ld_bank, const float* scales, int64_t row0,
+                          const double* __restrict__ w, int64_t nb, double* sigmasq, float* inv_sigma) {
+  const int64_t t = row0 + blockIdx.x;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
+    const double wk = w[k];
+    if (wk != 0.0) {
+      const float2 h = BankElem<BT>::get(bank, t * ld_bank + k);
+      acc += wk * ((double)h.x * h.x + (double)h.y * h.y);
+    }
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      const double sc = scales ? (double)scales[t] : 1.0;
+      const double s2 = v * sc * sc;  // sigma^2 of the dequantised template
+      sigmasq[t] = s2;
+      inv_sigma[t] = s2 > 0.0 ? (float)(sc / sqrt(s2)) : 0.0f;  // scale folded in: z is of the stored values
+    }
+  }
+}
+
+// --- compaction of window maxima ------------------------------------------
+
+struct TrigRec {
+  int32_t det, tmpl;
+  int64_t sample;
+  float snr, phase;
+};
+static_assert(sizeof(TrigRec) == 24, "mf_trigger layout");
+
+constexpr int kCompactBlock = 1024;        // threads
+constexpr int kCompactPerThread = 4;       // slots per thread
+constexpr int kCompactSpan = kCompactBlock * kCompactPerThread;
+
+__global__ void k_compact_count(const unsigned long long* __restrict__ slots, int64_t n_slots, int64_t* bc) {
+  const int64_t base = (int64_t)blockIdx.x * kCompactSpan;
+  int cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kCompactPerThread; ++i) {
+    const int64_t idx = base + (int64_t)i * kCompactBlock + threadIdx.x;
+    if (idx < n_slots && slots[idx] != 0ull) ++cnt;
+  }
+  __shared__ int red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = red[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) bc[blockIdx.x] = v;
+  }
+}
+
+// single block: exclusive scan of bc[0..n) in place, total -> *count
+__global__ void k_scan_blocks(int64_t* bc, int64_t n, int64_t* count) {
+  __shared__ int64_t carry;
+  __shared__ int64_t wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < n ? bc[i] : 0;
+    int64_t x = v;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      wsum[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t incl = x + (wid > 0 ? wsum[wid - 1] : 0);
+    if (i < n) bc[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void k_compact_write(const unsigned long long* __restrict__ slots, int64_t n_slots, int64_t n_sel,
+                                int64_t n_win, int64_t window, const int32_t* __restrict__ sel,
+                                const int64_t* __restrict__ bc, TrigRec* out, int64_t cap) {
+  const int64_t base = (int64_t)blockIdx.x * kCompactSpan;
+  __shared__ int wcount[32];
+  __shared__ int tot;
+  __shared__ int64_t run;
+  if (threadIdx.x == 0) run = bc[blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < kCompactPerThread; ++i) {
+    const int64_t idx = base + (int64_t)i * kCompactBlock + threadIdx.x;
+    const unsigned long long key = idx < n_slots ? slots[idx] : 0ull;
+    const bool has = key != 0ull;
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    if (lane == 0) wcount[wid] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int v = wcount[threadIdx.x];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      wcount[threadIdx.x] = x - v;  // exclusive
+      if (threadIdx.x == 31) tot = x;
+    }
+    __syncthreads();
+    if (has) {
+      const int64_t pos = run + wcount[wid] + __popc(m & ((1u << lane) - 1u));
+      if (pos < cap) {
+        const int64_t w = idx % n_win;
+        const int64_t ds = idx / n_win;
+        const int64_t p = ds % n_sel;
+        const int d = (int)(ds / n_sel);
+        const uint32_t lo = (uint32_t)(key & 0xffffffffull);
+        const int64_t n = (int64_t)(((1u << kSampleBits) - 1u) - (lo >> kPhaseBits));
+        const float r2 = __uint_as_float((uint32_t)(key >> 32));
+        const float ph = ((float)(lo & 2047u) / 2048.0f - 0.5f) * 6.283185307179586f;
+        (void)w;
+        (void)window;
+        out[pos] = TrigRec{d, sel[p], n, sqrtf(r2), ph};
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) run += tot;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_prep(const float2* dtilde, int64_t ld_d, const double* w, int64_t nb, int n_det,
+                        float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st) {
+  const int g = num_sms() * 4;
+  k_prep<<<g, 256, 0, st>>>(dtilde, ld_d, w, nb, n_det, q, ld_q);
+  ++g_launches;
+  if (slots && n_slots > 0) {
+    k_zero_u64<<<g, 256, 0, st>>>(slots, n_slots);
+    ++g_launches;
+  }
+  return cudaGetLastError();
+}
+
+int64_t launch_count() { return g_launches; }
+void add_launches(int64_t n) { g_launches += n; }
+
+cudaError_t launch_filter_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH_N(a.n, run_pass1_bt, (a, st)) }
+
+cudaError_t launch_filter_pass2(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH_N(a.n, run_pass2, (a, st)) }
+
+cudaError_t launch_filter_batch(const FilterArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_filter_pass1(a, st);
+  if (e != cudaSuccess) return e;
+  return launch_filter_pass2(a, st);
+}
+
+cudaError_t launch_rfft(const float* x, int64_t ld_s, int n_det, int64_t n, int n1, int n2, double dt,
+                        float2* scratch, float2* out, int64_t ld_d, cudaStream_t st) {
+  (void)n1;
+  (void)n2;
+  MF_DISPATCH_N(n, run_rfft, (x, ld_s, n_det, dt, scratch, out, ld_d, st))
+}
+
+cudaError_t launch_sigmasq(const void* bank, int bank_type, int64_t ld_bank, const float* scales, int64_t row0,
+                           int64_t n_rows, const double* w, int64_t nb, double* sigmasq, float* inv_sigma,
+                           cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  if (n_rows > 0x7fffffff) return cudaErrorInvalidValue;
+  switch (bank_type) {
+    case kBankF32:
+      k_sigmasq<kBankF32><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      break;
+    case kBankF16:
+      k_sigmasq<kBankF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      break;
+    case kBankBF16:
+      k_sigmasq<kBankBF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+int64_t compact_blocks(int64_t n_slots) { return (n_slots + kCompactSpan - 1) / kCompactSpan; }
+
+cudaError_t launch_compact(const unsigned long long* slots, int n_det, int64_t n_sel, int64_t n_win, int64_t window,
+                           const int32_t* sel, void* trig_out, int64_t trig_cap, int64_t* count, int64_t* bc,
+                           int64_t n_blocks_cap, cudaStream_t st) {
+  const int64_t n_slots = (int64_t)n_det * n_sel * n_win;
+  const int64_t nblk = compact_blocks(n_slots);
+  if (nblk > n_blocks_cap || nblk > 0x7fffffff) return cudaErrorInvalidValue;
+  if (nblk == 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), st);
+  k_compact_count<<<(unsigned)nblk, kCompactBlock, 0, st>>>(slots, n_slots, bc);
+  k_scan_blocks<<<1, 1024, 0, st>>>(bc, nblk, count);
+  k_compact_write<<<(unsigned)nblk, kCompactBlock, 0, st>>>(slots, n_slots, n_sel, n_win, window, sel, bc,
+                                                            reinterpret_cast<TrigRec*>(trig_out), trig_cap);
+  g_launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(const float2* in, int64_t ld_in, float2* out, int64_t ld_out, int64_t nb_out, int n_det,
+                            cudaStream_t st);
+
+}  // namespace mf

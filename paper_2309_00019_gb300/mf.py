@@ -1,0 +1,256 @@
+"""ctypes binding of libmf (include/mf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the matched filter runs in the CUDA
+kernels of libmf.so.  Device buffers are passed as integer addresses
+(``torch.Tensor.data_ptr()``), streams as ``torch.cuda.Stream.cuda_stream``.
+There is no CPU fallback: ``load()`` raises if the shared library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ESTATE, MF_EOVERFLOW, MF_ETIMEOUT = range(7)
+MF_F32, MF_F16, MF_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_ESTATE", 5: "MF_EOVERFLOW",
+                6: "MF_ETIMEOUT"}
+
+
+class mf_plan_desc(C.Structure):
+    _fields_ = [("fs", C.c_double), ("n", C.c_int64), ("n_det", C.c_int32), ("f_low", C.c_double),
+                ("f_high", C.c_double), ("dtype", C.c_int), ("snr_thr", C.c_double), ("window", C.c_int64),
+                ("valid_begin", C.c_int64), ("valid_end", C.c_int64), ("max_triggers", C.c_int64),
+                ("cuda_stream", C.c_void_p)]
+
+
+class mf_trigger(C.Structure):
+    _fields_ = [("det", C.c_int32), ("tmpl", C.c_int32), ("sample", C.c_int64), ("snr", C.c_float),
+                ("phase", C.c_float)]
+
+
+class mf_coinc_desc(C.Structure):
+    _fields_ = [("shift_samples", C.c_int64), ("n_shifts", C.c_int32), ("window_samples", C.c_int64),
+                ("rho_c_thr", C.c_double), ("rho_c_store", C.c_double), ("max_coincs", C.c_int64)]
+
+
+class mf_coinc(C.Structure):
+    _fields_ = [("tmpl", C.c_int32), ("shift", C.c_int32), ("sample0", C.c_int64), ("sample1", C.c_int64),
+                ("snr0", C.c_float), ("snr1", C.c_float), ("rho_c", C.c_float), ("reserved", C.c_int32)]
+
+
+class mf_plan_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("pass1_launches", C.c_int64), ("pass1_series", C.c_int64),
+                ("pass1_ms", C.c_double), ("pass2_launches", C.c_int64), ("pass2_series", C.c_int64),
+                ("pass2_ms", C.c_double)]
+
+
+TRIGGER_NP = np.dtype([("det", np.int32), ("tmpl", np.int32), ("sample", np.int64), ("snr", np.float32),
+                       ("phase", np.float32)])
+COINC_NP = np.dtype([("tmpl", np.int32), ("shift", np.int32), ("sample0", np.int64), ("sample1", np.int64),
+                     ("snr0", np.float32), ("snr1", np.float32), ("rho_c", np.float32), ("reserved", np.int32)])
+assert TRIGGER_NP.itemsize == C.sizeof(mf_trigger) == 24
+assert COINC_NP.itemsize == C.sizeof(mf_coinc) == 40
+
+_P = C.c_void_p
+_I64 = C.c_int64
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "mf_plan": (C.c_int, [C.POINTER(_P), C.POINTER(mf_plan_desc)]),
+    "mf_destroy": (None, [_P]),
+    "mf_last_error": (C.c_char_p, [_P]),
+    "mf_set_psd": (C.c_int, [_P, _P, _I64]),
+    "mf_load_bank": (C.c_int, [_P, _P, C.c_int, _I64, _I64, _P, C.c_int]),
+    "mf_bank_reserve": (C.c_int, [_P, C.c_int, _I64]),
+    "mf_bank_set_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, _P, C.c_int]),
+    "mf_get_sigmasq": (C.c_int, [_P, _P, _I64]),
+    "mf_strain_to_fd": (C.c_int, [_P, _P, _I64, _P, _I64]),
+    "mf_decimate": (C.c_int, [_P, _P, _I64, _P, _I64]),
+    "mf_filter": (C.c_int, [_P, _P, _I64, _P, _I64]),
+    "mf_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
+    "mf_device_triggers": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
+    "mf_coincide": (C.c_int, [_P, C.POINTER(mf_coinc_desc), _P]),
+    "mf_get_coincs": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
+    "mf_set_nbhd": (C.c_int, [_P, _P, _P, _I64, C.c_int]),
+    "mf_nbhd_union": (C.c_int, [_P, _P, _P, C.POINTER(_I64)]),
+    "mf_profile": (C.c_int, [_P, C.c_int]),
+    "mf_get_stats": (C.c_int, [_P, C.POINTER(mf_plan_stats), C.c_int]),
+}
+
+_lib = None
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path=LIB_PATH):
+    """Load libmf.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"libmf.so not found at {path}: build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(plan, st, ok=(MF_OK,)):
+    if st not in ok:
+        msg = load().mf_last_error(plan)
+        raise MFError(st, msg.decode() if msg else "")
+    return st
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+class Plan:
+    """Owner of one ``mf_plan_t``; methods mirror the C calls."""
+
+    def __init__(self, fs, n, n_det, f_low, f_high, snr_thr, window, valid_begin=0, valid_end=None,
+                 dtype=MF_F32, max_triggers=1 << 20, stream=None):
+        lib = load()
+        d = mf_plan_desc(fs=fs, n=n, n_det=n_det, f_low=f_low, f_high=f_high, dtype=dtype, snr_thr=snr_thr,
+                         window=window, valid_begin=valid_begin, valid_end=n if valid_end is None else valid_end,
+                         max_triggers=max_triggers, cuda_stream=stream)
+        h = _P()
+        _check(None, lib.mf_plan(C.byref(h), C.byref(d)))
+        self.h = h
+        self.desc = d
+        self.n, self.nb, self.n_det, self.n_tmpl = n, n // 2 + 1, n_det, 0
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_psd(self, psd):
+        psd = np.ascontiguousarray(psd, dtype=np.float64)
+        _check(self.h, self.lib.mf_set_psd(self.h, psd.ctypes.data, len(psd)))
+
+    def load_bank(self, htilde, dtype=MF_F32, ld=None, scales=None, on_device=None):
+        n_tmpl = htilde.shape[0]
+        ld = htilde.shape[1] if ld is None else ld
+        if on_device is None:
+            on_device = 0 if isinstance(htilde, np.ndarray) else int(htilde.is_cuda)
+        sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+        _check(self.h, self.lib.mf_load_bank(self.h, _ptr(htilde), dtype, n_tmpl, ld, _ptr(sc), on_device))
+        self.n_tmpl = n_tmpl
+
+    def bank_reserve(self, n_tmpl, dtype=MF_F32):
+        _check(self.h, self.lib.mf_bank_reserve(self.h, dtype, n_tmpl))
+        self.n_tmpl = n_tmpl
+
+    def bank_set_rows(self, row0, rows, ld=None, scales=None, on_device=None):
+        ld = rows.shape[1] if ld is None else ld
+        if on_device is None:
+            on_device = 0 if isinstance(rows, np.ndarray) else int(rows.is_cuda)
+        sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+        _check(self.h, self.lib.mf_bank_set_rows(self.h, row0, rows.shape[0], _ptr(rows), ld, _ptr(sc), on_device))
+
+    def sigmasq(self, n=None):
+        n = self.n_tmpl if n is None else n
+        out = np.zeros(n, dtype=np.float64)
+        _check(self.h, self.lib.mf_get_sigmasq(self.h, out.ctypes.data, n))
+        return out
+
+    def strain_to_fd(self, strain, dtilde, ld_strain=None, ld_dtilde=None):
+        ld_strain = strain.shape[-1] if ld_strain is None else ld_strain
+        ld_dtilde = dtilde.shape[-1] if ld_dtilde is None else ld_dtilde
+        _check(self.h, self.lib.mf_strain_to_fd(self.h, _ptr(strain), ld_strain, _ptr(dtilde), ld_dtilde))
+
+    def decimate(self, dtilde_in, dtilde_out, ld_in=None, ld_out=None):
+        ld_in = dtilde_in.shape[-1] if ld_in is None else ld_in
+        ld_out = dtilde_out.shape[-1] if ld_out is None else ld_out
+        _check(self.h, self.lib.mf_decimate(self.h, _ptr(dtilde_in), ld_in, _ptr(dtilde_out), ld_out))
+
+    def filter(self, dtilde, subset=None, n_subset=None, ld=None):
+        ld = dtilde.shape[-1] if ld is None else ld
+        if subset is None:
+            n_subset = -1
+        elif n_subset is None:
+            n_subset = subset.shape[0]
+        sp = _ptr(subset) if (subset is not None and n_subset > 0) else None
+        _check(self.h, self.lib.mf_filter(self.h, _ptr(dtilde), ld, sp, n_subset))
+
+    def triggers(self, cap=None):
+        n = _I64(0)
+        if cap is None:
+            _check(self.h, self.lib.mf_get_triggers(self.h, None, 0, C.byref(n)), ok=(MF_OK, MF_EOVERFLOW))
+            cap = n.value
+        out = np.zeros(cap, dtype=TRIGGER_NP)
+        st = self.lib.mf_get_triggers(self.h, out.ctypes.data if cap else None, cap, C.byref(n))
+        _check(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
+        return out[: min(cap, n.value, self.desc.max_triggers)], n.value, st
+
+    def device_triggers(self):
+        t, c = _P(), _P()
+        _check(self.h, self.lib.mf_device_triggers(self.h, C.byref(t), C.byref(c)))
+        return t.value, c.value
+
+    def coincide(self, followed, shift_samples, n_shifts, window_samples, rho_c_thr, rho_c_store=None,
+                 max_coincs=1 << 20):
+        d = mf_coinc_desc(shift_samples=shift_samples, n_shifts=n_shifts, window_samples=window_samples,
+                          rho_c_thr=rho_c_thr, rho_c_store=rho_c_thr if rho_c_store is None else rho_c_store,
+                          max_coincs=max_coincs)
+        _check(self.h, self.lib.mf_coincide(self.h, C.byref(d), _ptr(followed)))
+        self.coinc_cap = max(getattr(self, "coinc_cap", 0), max_coincs)
+
+    def coincs(self, cap=None):
+        n = _I64(0)
+        if cap is None:
+            _check(self.h, self.lib.mf_get_coincs(self.h, None, 0, C.byref(n)), ok=(MF_OK, MF_EOVERFLOW))
+            cap = n.value
+        out = np.zeros(cap, dtype=COINC_NP)
+        st = self.lib.mf_get_coincs(self.h, out.ctypes.data if cap else None, cap, C.byref(n))
+        _check(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
+        return out[: min(cap, n.value, getattr(self, "coinc_cap", cap))], n.value, st
+
+    def set_nbhd(self, ptr, idx):
+        ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        _check(self.h, self.lib.mf_set_nbhd(self.h, ptr.ctypes.data, idx.ctypes.data if len(idx) else None,
+                                            len(ptr) - 1, 0))
+
+    def nbhd_union(self, followed, subset):
+        n = _I64(0)
+        _check(self.h, self.lib.mf_nbhd_union(self.h, _ptr(followed), _ptr(subset), C.byref(n)))
+        return n.value
+
+    def profile(self, enable=True):
+        _check(self.h, self.lib.mf_profile(self.h, int(enable)))
+
+    def stats(self, reset=False):
+        st = mf_plan_stats()
+        _check(self.h, self.lib.mf_get_stats(self.h, C.byref(st), int(reset)))
+        return {f: getattr(st, f) for f, _ in mf_plan_stats._fields_}

@@ -22,6 +22,7 @@ from .generators import (  # noqa: F401
     taylorf2_phase,
     taylorf2,
     taylorf2_torch,
+    taylorf2_chunks_torch,
     coloured_noise_fd,
     sine_gaussian,
     sine_gaussian_amplitude,

@@ -384,3 +384,20 @@ def nbhd_map(c_m1, c_m2, f_m1, f_m2, f0, f_low, f_high, min_match=0.9, max_size=
     idx = np.concatenate(idx_l) if idx_l else np.zeros(0, np.int32)
     val = np.concatenate(val_l) if val_l else np.zeros(0)
     return ptr, idx, val
+
+
+def taylorf2_chunks_torch(n, fs, m1, m2, f_low, device, chunk=128, ld=None):
+    """Yield (row0, complex64 device tensor [rows, ld]) blocks of a TaylorF2 bank
+    generated on ``device`` (see ``taylorf2_torch``); the tensor is reused."""
+    import torch
+
+    nb = n // 2 + 1
+    ld = nb if ld is None else ld
+    buf = None
+    for r0 in range(0, len(m1), chunk):
+        r1 = min(len(m1), r0 + chunk)
+        if buf is None or buf.shape[0] != r1 - r0:
+            buf = torch.zeros((r1 - r0, ld), dtype=torch.complex64, device=device)
+        taylorf2_torch(n, fs, m1[r0:r1], m2[r0:r1], f_low, device, out=buf, ld=ld)
+        torch.cuda.synchronize(device)
+        yield r0, buf
