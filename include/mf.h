@@ -151,13 +151,16 @@ mf_status mf_device_triggers(mf_plan_t plan, const mf_trigger** trig, const int6
  * the plan's stream (up to 1024 batches between reads): pass1_* is the
  * product + column-transform kernel, pass2_* the row-transform + SNR /
  * threshold / window-max kernel; *_series = (template, detector) series they
- * processed, *_ms = summed device time. */
+ * processed, *_ms = summed device time; fused_* the same for the persistent
+ * kernel that runs both passes of all batches of one mf_filter in one launch. */
 typedef struct {
   int64_t launches;
   int64_t pass1_launches, pass1_series;
   double pass1_ms;
   int64_t pass2_launches, pass2_series;
   double pass2_ms;
+  int64_t fused_launches, fused_series;  /* single-launch filter (both passes, every batch) */
+  double fused_ms;
 } mf_plan_stats;
 
 /* Turn event profiling of the filter kernels on (enable != 0) or off. */

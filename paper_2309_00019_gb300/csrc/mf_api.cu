@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -61,6 +62,15 @@ struct mf_plan_s {
   int64_t flags_cap = 0;
   int64_t* ubc = nullptr;
   int64_t* ucount = nullptr;
+  // TMA-staged filter
+  mf::Filter2Maps maps;
+  bool maps_valid = false;
+  int impl = 2;             // 1: per-thread loads, 2: TMA-staged per batch, 3: fused persistent, 4: register-pipelined
+  int fz_B = 1, fz_slots = 3;   // fused schedule: templates per batch, scratch slots
+  unsigned* fz_counters = nullptr;
+  int64_t fz_counters_cap = 0;
+  int* status = nullptr;    // device status word
+  float2* tw = nullptr;     // sub-FFT twiddle tables [2][1024]
   // instrumentation
   mf_plan_stats stats{};
   bool prof = false;
@@ -214,18 +224,35 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   p->ld_q = (p->nb + 63) / 64 * 64;
   // batch of templates per pass pair: keep the pass-1 -> pass-2 scratch within ~64 MB (L2 resident)
   const int64_t per = (int64_t)d.n_det * d.n * (int64_t)sizeof(float2);
-  p->batch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t(64) << 20) / per, 4096));
+  int64_t budget = int64_t(128) << 20;
+  if (const char* b = std::getenv("MF_SCRATCH_MB")) budget = std::max<int64_t>(1, std::atoll(b)) << 20;
+  p->batch = (int)std::max<int64_t>(1, std::min<int64_t>(budget / per, 4096));
+  if (const char* v = std::getenv("MF_FILTER_IMPL")) p->impl = std::atoi(v);
+  if (p->impl < 1 || p->impl > 4) p->impl = 2;
+  if (p->impl == 3 && !mf::fused_supported(d.n)) p->impl = 2;
+  if (const char* v = std::getenv("MF_FUSED_SLOTS")) p->fz_slots = std::max(2, std::atoi(v));
+  p->fz_B = (int)std::max<int64_t>(1, std::min<int64_t>(budget / (per * p->fz_slots), 4096));
+  if (const char* v = std::getenv("MF_FUSED_B")) p->fz_B = std::max(1, std::atoi(v));
+  const int64_t scratch_series = std::max<int64_t>(p->batch, (int64_t)p->fz_B * p->fz_slots);
   mf_status s;
   if ((s = dalloc(p, &p->w_dev, p->nb * sizeof(double), "weights")) != MF_OK ||
       (s = dalloc(p, &p->q, (size_t)d.n_det * p->ld_q * sizeof(float2), "weighted data")) != MF_OK ||
-      (s = dalloc(p, &p->scratch, (size_t)p->batch * per, "scratch")) != MF_OK ||
+      (s = dalloc(p, &p->scratch, (size_t)scratch_series * per, "scratch")) != MF_OK ||
       (s = dalloc(p, &p->trig, (size_t)d.max_triggers * sizeof(mf_trigger), "triggers")) != MF_OK ||
-      (s = dalloc(p, &p->count, sizeof(int64_t), "count")) != MF_OK) {
+      (s = dalloc(p, &p->count, sizeof(int64_t), "count")) != MF_OK ||
+      (s = dalloc(p, &p->status, sizeof(int), "status")) != MF_OK ||
+      (s = dalloc(p, &p->tw, 2 * 1024 * sizeof(float2), "twiddles")) != MF_OK) {
     g_err = p->err;
     mf_destroy(p);
     return s;
   }
   cudaMemsetAsync(p->count, 0, sizeof(int64_t), p->st);
+  cudaMemsetAsync(p->status, 0, sizeof(int), p->st);
+  if (mf::launch_fill_twiddles(d.n, p->tw, p->tw + 1024, p->st) != cudaSuccess) {
+    g_err = "mf_plan: twiddle table kernel";
+    mf_destroy(p);
+    return MF_ECUDA;
+  }
   *out = p;
   return MF_OK;
 }
@@ -236,7 +263,7 @@ void mf_destroy(mf_plan_t p) {
   dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev);
   dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
-  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount);
+  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->fz_counters);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
 }
@@ -259,6 +286,7 @@ mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
   if (n_tmpl < 1 || n_tmpl > 0x7fffffff) return fail(p, MF_EINVAL, "mf_bank_reserve: n_tmpl must be in [1, 2^31)");
   cudaStreamSynchronize(p->st);
   p->n_tmpl = 0;
+  p->maps_valid = false;
   p->bank_dtype = dtype;
   p->ld_bank = (p->nb + 63) / 64 * 64;
   const size_t bytes = (size_t)n_tmpl * p->ld_bank * elem_bytes(dtype);
@@ -391,18 +419,74 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.n_win = p->n_win;
   a.n_sel_total = n_sel;
   a.slots = p->slots;
+  a.status = p->status;
+  a.tw1 = p->tw;
+  a.tw2 = p->tw + 1024;
+  if (p->impl != 1 && !p->maps_valid) {
+    e = mf::filter2_encode_maps(a, p->n_tmpl, &p->maps);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter tensor maps");
+    p->maps_valid = true;
+  }
   LaunchScope ls(p);
   ls.before = launches_before;
-  for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
+  if (p->impl == 3 && n_sel > 0) {
+    // one persistent launch for every batch and both passes
+    mf::FusedSched q{};
+    q.B = p->fz_B;
+    q.nb = (int)((n_sel + q.B - 1) / q.B);
+    q.n_slots = p->fz_slots;
+    q.n_det = p->d.n_det;
+    int i1 = 0, i2 = 0;
+    mf::fused_items(p->d.n, &i1, &i2);
+    const int64_t last = n_sel - (int64_t)(q.nb - 1) * q.B;
+    q.F1 = q.B * q.n_det * i1;
+    q.F2 = q.B * q.n_det * i2;
+    q.L1 = (int)last * q.n_det * i1;
+    q.L2 = (int)last * q.n_det * i2;
+    const int64_t total = (int64_t)(q.nb - 1) * (q.F1 + q.F2) + q.L1 + q.L2;
+    if (total > 0x7fffffff) return fail(p, MF_EINVAL, "mf_filter: selection too large for one launch");
+    q.total = (int)total;
+    const int64_t need = 1 + 2 * (int64_t)q.nb;
+    if (need > p->fz_counters_cap) {
+      mf_status s2 = dalloc(p, &p->fz_counters, (size_t)need * sizeof(unsigned), "fused counters");
+      if (s2 != MF_OK) {
+        p->fz_counters_cap = 0;
+        return s2;
+      }
+      p->fz_counters_cap = need;
+    }
+    e = cudaMemsetAsync(p->fz_counters, 0, need * sizeof(unsigned), p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter counters");
+    q.head = p->fz_counters;
+    q.done1 = p->fz_counters + 1;
+    q.done2 = p->fz_counters + 1 + q.nb;
+    a.pos0 = 0;
+    a.count = (int)std::min<int64_t>(n_sel, 0x7fffffff);
+    const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
+    const int e0 = prof ? (int)p->samples.size() * 3 : 0;
+    if (prof) cudaEventRecord(p->ev[e0], p->st);
+    e = mf::launch_filter_fused(a, p->maps, q, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter fused kernel");
+    if (prof) {
+      cudaEventRecord(p->ev[e0 + 1], p->st);
+      cudaEventRecord(p->ev[e0 + 2], p->st);
+      p->samples.push_back({e0, -n_sel * p->d.n_det});  // negative: one fused launch covering both passes
+    }
+  }
+  for (int64_t pos0 = 0; p->impl != 3 && pos0 < n_sel; pos0 += p->batch) {
     a.pos0 = pos0;
     a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
     const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
     const int e0 = prof ? (int)p->samples.size() * 3 : 0;
     if (prof) cudaEventRecord(p->ev[e0], p->st);
-    e = mf::launch_filter_pass1(a, p->st);
+    e = p->impl == 1   ? mf::launch_filter_pass1(a, p->st)
+        : p->impl == 4 ? mf::launch_filter4_pass1(a, p->st)
+                       : mf::launch_filter2_pass1(a, p->maps, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 1");
     if (prof) cudaEventRecord(p->ev[e0 + 1], p->st);
-    e = mf::launch_filter_pass2(a, p->st);
+    e = p->impl == 1   ? mf::launch_filter_pass2(a, p->st)
+        : p->impl == 4 ? mf::launch_filter4_pass2(a, p->st)
+                       : mf::launch_filter2_pass2(a, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 2");
     if (prof) {
       cudaEventRecord(p->ev[e0 + 2], p->st);
@@ -440,6 +524,12 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     e = cudaEventElapsedTime(&t1, p->ev[sm.e0], p->ev[sm.e0 + 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, p->ev[sm.e0 + 1], p->ev[sm.e0 + 2]);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_stats elapsed");
+    if (sm.series < 0) {  // fused launch: both passes in one kernel
+      p->stats.fused_launches += 1;
+      p->stats.fused_series += -sm.series;
+      p->stats.fused_ms += t1;
+      continue;
+    }
     p->stats.pass1_launches += 1;
     p->stats.pass1_series += sm.series;
     p->stats.pass1_ms += t1;
@@ -461,6 +551,13 @@ mf_status mf_get_triggers(mf_plan_t p, mf_trigger* out, int64_t cap, int64_t* n_
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_triggers count");
   *n_found = n;
+  int dst = 0;
+  e = cudaMemcpy(&dst, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_triggers status");
+  if (dst != 0) {
+    cudaMemset(p->status, 0, sizeof(int));
+    return fail(p, MF_ETIMEOUT, "mf_get_triggers: a bounded device wait timed out; results are incomplete");
+  }
   const int64_t m = std::min<int64_t>(std::min<int64_t>(n, cap), p->d.max_triggers);
   if (m > 0) {
     e = cudaMemcpyAsync(out, p->trig, m * sizeof(mf_trigger), cudaMemcpyDeviceToHost, p->st);

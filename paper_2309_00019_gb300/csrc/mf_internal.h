@@ -2,6 +2,7 @@
 // kernels (mf_kernels.cu, mf_glue.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,7 +43,42 @@ struct FilterArgs {
   int64_t n_win;
   int64_t n_sel_total;      // slots are [n_det][n_sel_total][n_win]
   unsigned long long* slots;
+  int* status;              // device status word (bounded waits report here)
+  const float2* tw1;        // sub-FFT twiddle tables (w_N1^{r j}, w_N2^{r j}), 8 KB max each
+  const float2* tw2;
 };
+
+// Tensor maps of the TMA-staged filter: template bank and weighted data, each
+// viewed as [depth][N1/2 rows k1][N2 columns k2].
+struct Filter2Maps {
+  CUtensorMap h;
+  CUtensorMap q;
+  bool ok = false;
+};
+cudaError_t filter2_encode_maps(const FilterArgs& a, int64_t n_tmpl, Filter2Maps* m);
+cudaError_t launch_filter2_pass1(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st);
+cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);
+// register-pipelined variant of the two passes (direct loads, no staging)
+cudaError_t launch_filter4_pass1(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_filter4_pass2(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st);
+
+// Schedule of the fused persistent filter (both passes of every batch in one
+// launch).  The selection is cut into nb batches of B templates (the last one
+// may be short); F1/F2 (L1/L2) are the pass-1/pass-2 items of a full (the
+// last) batch; scratch holds n_slots batches; head/done1/done2 are zeroed
+// device counters (done1/done2 of length nb).
+struct FusedSched {
+  int B, nb, n_slots, n_det;
+  int F1, F2, L1, L2;
+  int total;
+  unsigned* head;
+  unsigned* done1;
+  unsigned* done2;
+};
+bool fused_supported(int64_t n);
+void fused_items(int64_t n, int* p1_per_series, int* p2_per_series);
+cudaError_t launch_filter_fused(const FilterArgs& a, const Filter2Maps& m, const FusedSched& q, cudaStream_t st);
 
 // Number of kernels launched by this library (all plans, all threads).
 int64_t launch_count();

@@ -15,25 +15,13 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "mf_fft.cuh"
-#include "mf_internal.h"
+#include "mf_common.cuh"
 
 namespace mf {
 
 namespace {
 
 constexpr int kThreads = 256;
-
-// Shared-memory stride of one column/row: >= pad and congruent to L (mod 16),
-// where L = consecutive-thread lanes a group contributes to a half-warp, so
-// 64-bit shared accesses of a half-warp hit 16 distinct bank pairs.
-constexpr int stride_for(int pad, int lanes) {
-  int L = lanes >= 16 ? 0 : lanes;
-  int s = pad;
-  if (L == 0) return s;
-  while (s % 16 != L) ++s;
-  return s;
-}
 
 template <int N1>
 struct P1Geo {
@@ -67,29 +55,6 @@ __device__ __forceinline__ void twiddle_run(float2 (&u)[R], float2 b) {
 // ---------------------------------------------------------------------------
 // loaders (pass 1 input) and epilogues (pass 2 output)
 // ---------------------------------------------------------------------------
-
-template <int BT>
-struct BankElem;
-template <>
-struct BankElem<kBankF32> {
-  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
-    return __ldg(reinterpret_cast<const float2*>(p) + i);
-  }
-};
-template <>
-struct BankElem<kBankF16> {
-  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
-    __half2 h = __ldg(reinterpret_cast<const __half2*>(p) + i);
-    return __half22float2(h);
-  }
-};
-template <>
-struct BankElem<kBankBF16> {
-  __device__ __forceinline__ static float2 get(const void* p, int64_t i) {
-    __nv_bfloat162 h = __ldg(reinterpret_cast<const __nv_bfloat162*>(p) + i);
-    return __bfloat1622float2(h);
-  }
-};
 
 // x[k] = q_d[k] conj(h_t[k]); series s = b * n_det + d, template t = sel[pos0 + b]
 template <int BT>
@@ -129,38 +94,6 @@ struct RealLoad {
   __device__ __forceinline__ Ser series(int s) const { return Ser{x + (int64_t)s * ld}; }
   __device__ __forceinline__ float2 value(const Ser& se, int64_t k) const {
     return make_float2(__ldg(se.xd + k), 0.f);
-  }
-};
-
-struct FilterEpi {
-  const int32_t* sel;
-  const float* inv_sigma;
-  int64_t pos0;
-  int n_det;
-  float thr2;
-  int64_t window, vb, ve, n_win, n_sel_total;
-  unsigned long long* slots;
-  struct Ser {
-    float is;
-    unsigned long long* slot;
-  };
-  __device__ __forceinline__ Ser series(int s) const {
-    const int d = s % n_det;
-    const int64_t pos = pos0 + s / n_det;
-    return Ser{__ldg(inv_sigma + sel[pos]), slots + ((int64_t)d * n_sel_total + pos) * n_win};
-  }
-  __device__ __forceinline__ void operator()(const Ser& se, int64_t n, float2 z) const {
-    const float a = z.x * se.is, b = z.y * se.is;
-    const float r2 = fmaf(a, a, b * b);
-    if (r2 >= thr2) {
-      if (n < vb || n >= ve) return;
-      const float ph = atan2f(b, a);
-      const uint32_t code = (uint32_t)__float2int_rn(fmaf(ph, 0.15915494309189535f, 0.5f) * 2048.0f) & 2047u;
-      const unsigned long long key = ((unsigned long long)__float_as_uint(r2) << 32) |
-                                     ((unsigned long long)(((1u << kSampleBits) - 1u) - (uint32_t)n) << kPhaseBits) |
-                                     code;
-      atomicMax(se.slot + n / window, key);
-    }
   }
 };
 

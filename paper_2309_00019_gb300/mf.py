@@ -47,7 +47,8 @@ class mf_coinc(C.Structure):
 class mf_plan_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pass1_launches", C.c_int64), ("pass1_series", C.c_int64),
                 ("pass1_ms", C.c_double), ("pass2_launches", C.c_int64), ("pass2_series", C.c_int64),
-                ("pass2_ms", C.c_double)]
+                ("pass2_ms", C.c_double), ("fused_launches", C.c_int64), ("fused_series", C.c_int64),
+                ("fused_ms", C.c_double)]
 
 
 TRIGGER_NP = np.dtype([("det", np.int32), ("tmpl", np.int32), ("sample", np.int64), ("snr", np.float32),
