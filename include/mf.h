@@ -214,6 +214,33 @@ mf_status mf_set_nbhd(mf_plan_t plan, const int64_t* ptr, const int32_t* idx, in
  * [n_tmpl of this plan]; *n_subset (host) receives the count.  Synchronises. */
 mf_status mf_nbhd_union(mf_plan_t plan, const int32_t* followed, int32_t* subset, int64_t* n_subset);
 
+/* ---- filtering without device allocation ------------------------------- */
+
+/* The filter of mf_filter (same arithmetic, threshold, window maxima and
+ * trigger order) for callers that cannot allocate GPU memory, e.g. code that
+ * runs inside another framework's memory pool, a loop that must never
+ * allocate, or a plug-in that is only handed buffers.  The paper has no
+ * counterpart: it is an interface convenience of this library.
+ *
+ * No plan, no allocation: all working memory lives in one 32 MiB __device__
+ * array compiled into the library (present on every GPU that loads it, until
+ * the process exits).  Limits: N a power of two in [2^12, 2^16], n_det 1 or 2,
+ * 1 <= n_tmpl <= 1024, at most 256 windows per segment; anything larger is
+ * rejected with MF_EINVAL.  The whole segment is analysed (valid range [0, N)).
+ *   psd:    device float64 [N/2+1], one-sided PSD (weights as in mf_set_psd)
+ *   htilde: device complex64 templates [n_tmpl][ld_h] (float32 pairs)
+ *   dtilde: device complex64 data [n_det][ld_d]
+ *   trig:   device mf_trigger [trig_cap] (out), count: device int64 (out) =
+ *           number found (may exceed trig_cap; only trig_cap are written)
+ * Asynchronous on cuda_stream.  All calls share the one array: calls that
+ * overlap on the GPU race, so serialise them.  The first call on a device
+ * looks up the array's device address, so make it before any stream capture.
+ * Errors are reported through mf_last_error(NULL). */
+mf_status mf_filter_noalloc(double fs, int64_t n, int32_t n_det, double f_low, double f_high, double snr_thr,
+                            int64_t window, const double* psd, const void* htilde, int64_t n_tmpl, int64_t ld_h,
+                            const void* dtilde, int64_t ld_d, mf_trigger* trig, int64_t trig_cap, int64_t* count,
+                            void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -192,6 +192,10 @@ mf_status ensure_slots(mf_plan_t p, int64_t n_sel) {
 
 }  // namespace
 
+namespace mf {
+void set_global_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace mf
+
 extern "C" {
 
 const char* mf_last_error(mf_plan_t plan) { return plan ? plan->err.c_str() : g_err.c_str(); }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mf {
 
 // Packed per-window maximum: [63:32] float bits of rho^2 (>= 0, so integer
@@ -79,6 +81,10 @@ struct FusedSched {
 bool fused_supported(int64_t n);
 void fused_items(int64_t n, int* p1_per_series, int* p2_per_series);
 cudaError_t launch_filter_fused(const FilterArgs& a, const Filter2Maps& m, const FusedSched& q, cudaStream_t st);
+
+// Message returned by mf_last_error(NULL) for calls without a plan.
+void set_global_error(const char* msg);
+inline void set_global_error(const std::string& msg) { set_global_error(msg.c_str()); }
 
 // Number of kernels launched by this library (all plans, all threads).
 int64_t launch_count();

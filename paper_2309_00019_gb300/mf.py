@@ -80,6 +80,8 @@ SIGNATURES = {
     "mf_set_nbhd": (C.c_int, [_P, _P, _P, _I64, C.c_int]),
     "mf_nbhd_union": (C.c_int, [_P, _P, _P, C.POINTER(_I64)]),
     "mf_profile": (C.c_int, [_P, C.c_int]),
+    "mf_filter_noalloc": (C.c_int, [C.c_double, _I64, C.c_int32, C.c_double, C.c_double, C.c_double, _I64, _P, _P,
+                                    _I64, _I64, _P, _I64, _P, _I64, _P, _P]),
     "mf_get_stats": (C.c_int, [_P, C.POINTER(mf_plan_stats), C.c_int]),
 }
 
