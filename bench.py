@@ -38,6 +38,28 @@ UNIT = "template-seconds/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# names of the two filter kernels per plan implementation (mf_plan_stats.impl)
+KERNEL_NAMES = {1: ("k_pass1", "k_pass2"), 2: ("k_cols", "k_rows"), 3: ("k_fused", "k_fused"),
+                4: ("k_cols4", "k_rows4")}
+
+
+def measured_traffic(kernel, series_per_launch):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries
+    (lines 'bench-traffic: <kernel> series=<s> dram_bytes=<b>'), or None."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    name = kernel.split(" ")[0].replace(" ", "")
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(d, fn)) as fh:
+            for line in fh:
+                if line.startswith("bench-traffic:"):
+                    f = line.split()
+                    if f[1] == name and int(f[2].split("=")[1]) == int(round(series_per_launch)):
+                        return int(f[3].split("=")[1])
+    return None
 
 
 def parse():
@@ -50,7 +72,41 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--kernel-case", type=int, default=0, metavar="LOG2N",
+                    help="instead of the benchmark, run two mf_filter calls on a 2-detector plan with N = 2^LOG2N "
+                         "(a small, fixed case for profiler captures) and exit")
+    ap.add_argument("--kernel-templates", type=int, default=16)
     return ap.parse_args()
+
+
+def kernel_case(lg, n_tmpl):
+    """Two filter calls of a 2-detector, n_tmpl-template plan at N = 2^lg (TaylorF2 bank,
+    coloured noise); used as the fixed workload of profiler captures."""
+    import torch
+
+    import synth
+    from paper_2309_00019_gb300 import _build, mf
+
+    if not os.path.exists(mf.LIB_PATH):
+        _build.build()
+    n = 1 << lg
+    fs = 2048.0 if lg >= 19 else 512.0
+    rng = np.random.default_rng(0)
+    dev = torch.device("cuda:0")
+    m1, m2 = synth.sample_bank_uniform_masses(rng, n_tmpl, 1.4, 10.0)
+    bank = synth.taylorf2_torch(n, fs, m1, m2, 30.0, dev)
+    fd = np.stack([synth.coloured_noise_fd(rng, n, fs) for _ in range(2)]).astype(np.complex64)
+    p = mf.Plan(fs, n, 2, 30.0, fs / 2, 4.0, int(fs))
+    p.set_psd(synth.psd_bins(n, fs))
+    p.load_bank(bank)
+    d = torch.from_numpy(fd).to(dev)
+    for _ in range(2):
+        p.filter(d)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": lg, "templates": n_tmpl, "triggers": p.triggers()[1],
+                      "impl": p.stats()["impl"], "batch": p.stats()["batch"]}))
+    p.close()
+    return 0
 
 
 def peaks():
@@ -186,6 +242,8 @@ def reference_arm(args, rank, world):
 
 def main():
     args = parse()
+    if args.kernel_case:
+        return kernel_case(args.kernel_case, args.kernel_templates)
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
@@ -272,32 +330,44 @@ def main():
 
     # dominant kernel (profiled launches of the timed region): ALU roofline and HBM view
     kinds = []
-    for name, s, n, nsub1, nsub2, nb in (("stage1", s1, hp.n1, None, None, hp.n1 // 2 + 1),
-                                         ("stage2", s2, hp.n2, None, None, hp.n2 // 2 + 1)):
+    for stage, s, n in (("stage1", s1, hp.n1), ("stage2", s2, hp.n2)):
         lg = int(round(math.log2(n)))
         n1s, n2s = 1 << ((lg + 1) // 2), 1 << (lg // 2)
-        for k, sub in (("pass1", n1s), ("pass2", n2s)):
+        names = KERNEL_NAMES.get(s["impl"], ("pass1", "pass2"))
+        nb = n // 2 + 1
+        if s["fused_launches"] > 0:
+            kinds.append(dict(kernel=f"k_fused<{n1s}> ({stage})", ms=s["fused_ms"], launches=s["fused_launches"],
+                              series=s["fused_series"], flops_series=5.0 * n * math.log2(n), n=n,
+                              tmpl_bytes_series=nb * 8 / hp.n_det))
+        for k, sub, nm in (("pass1", n1s, names[0]), ("pass2", n2s, names[1])):
             if s[f"{k}_launches"] > 0:
-                kinds.append(dict(name=f"{name}.{k}", ms=s[f"{k}_ms"], launches=s[f"{k}_launches"],
-                                  series=s[f"{k}_series"], n=n, sub=sub, nb=nb))
+                kinds.append(dict(kernel=f"{nm}<{n1s},{n2s}> ({stage})", ms=s[f"{k}_ms"],
+                                  launches=s[f"{k}_launches"], series=s[f"{k}_series"],
+                                  flops_series=5.0 * n * math.log2(sub), n=n,
+                                  tmpl_bytes_series=(nb * 8 / hp.n_det) if k == "pass1" else 0.0))
     dom = max(kinds, key=lambda d: d["ms"]) if kinds else None
     roof = None
     hbm_gbs, hbm_kind = peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    klist = []
+    for d in kinds:
+        per_ms = d["ms"] / d["launches"]
+        spl = d["series"] / d["launches"]
+        klist.append({"kernel": d["kernel"], "launches": d["launches"], "ms_total": d["ms"],
+                      "per_launch_ms": per_ms, "series_per_launch": spl,
+                      "alu_tflops": spl * d["flops_series"] / (per_ms * 1e-3) / 1e12,
+                      "template_gbs": spl * d["tmpl_bytes_series"] / (per_ms * 1e-3) / 1e9})
     if dom is not None:
         per_launch_ms = dom["ms"] / dom["launches"]
-        series_per_launch = dom["series"] / dom["launches"]
-        flops = series_per_launch * 5.0 * dom["n"] * math.log2(dom["sub"])
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        tmpl_bytes = series_per_launch / hp.n_det * dom["nb"] * 8 if dom["name"].endswith("pass1") else 0
+        spl = dom["series"] / dom["launches"]
+        achieved = spl * dom["flops_series"] / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": f"k_pass{dom['name'][-1]} ({dom['name']})",
-                "per_launch_ms": per_launch_ms, "series_per_launch": series_per_launch,
-                "flops_per_series": 5.0 * dom["n"] * math.log2(dom["sub"]),
+                "frac": achieved / alu_peak, "traffic": measured_traffic(dom["kernel"], spl),
+                "kernel": dom["kernel"], "per_launch_ms": per_launch_ms, "series_per_launch": spl,
+                "flops_per_series": dom["flops_series"],
+                "flop_convention": "5 N log2(M) per series for an N-point transform built from M-point sub-FFTs",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
-                "hbm_view": {"algorithmic_bytes_per_launch": tmpl_bytes,
-                             "achieved_gbs": tmpl_bytes / (per_launch_ms * 1e-3) / 1e9,
-                             "peak_gbs": hbm_gbs, "peak_kind": hbm_kind}}
+                "kernels": klist}
     # whole-step HBM view: template bytes the step must stream / step time
     step_bytes = (len(cfg.coarse_m1) * (hp.n1 // 2 + 1) + statistics.mean(unions) * (hp.n2 // 2 + 1)) * 8
     step_hbm = step_bytes / (t_dev / args.steps) / 1e9

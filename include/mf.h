@@ -161,6 +161,8 @@ typedef struct {
   double pass2_ms;
   int64_t fused_launches, fused_series;  /* single-launch filter (both passes, every batch) */
   double fused_ms;
+  int32_t impl;       /* filter kernels in use: 1 per-thread loads, 2 TMA-staged, 3 fused, 4 register-pipelined */
+  int32_t batch;      /* templates per pass pair (impl 1, 2, 4) or per fused batch (impl 3) */
 } mf_plan_stats;
 
 /* Turn event profiling of the filter kernels on (enable != 0) or off. */

@@ -542,6 +542,8 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     p->stats.pass2_ms += t2;
   }
   p->samples.clear();
+  p->stats.impl = p->impl;
+  p->stats.batch = p->impl == 3 ? p->fz_B : p->batch;
   *out = p->stats;
   if (reset) p->stats = mf_plan_stats{};
   return MF_OK;

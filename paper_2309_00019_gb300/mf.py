@@ -48,7 +48,7 @@ class mf_plan_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pass1_launches", C.c_int64), ("pass1_series", C.c_int64),
                 ("pass1_ms", C.c_double), ("pass2_launches", C.c_int64), ("pass2_series", C.c_int64),
                 ("pass2_ms", C.c_double), ("fused_launches", C.c_int64), ("fused_series", C.c_int64),
-                ("fused_ms", C.c_double)]
+                ("fused_ms", C.c_double), ("impl", C.c_int32), ("batch", C.c_int32)]
 
 
 TRIGGER_NP = np.dtype([("det", np.int32), ("tmpl", np.int32), ("sample", np.int64), ("snr", np.float32),

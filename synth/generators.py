@@ -189,12 +189,13 @@ def taylorf2(n, fs, m1, m2, f_low, t0=0.0, phi0=0.0, amp=1.0, dtype=np.complex12
     return out.astype(dtype)
 
 
-def taylorf2_torch(n, fs, m1, m2, f_low, device, out=None, ld=None):
+def taylorf2_torch(n, fs, m1, m2, f_low, device, out=None, ld=None, block=32):
     """Same waveform as ``taylorf2`` for many templates at once, evaluated with
     torch in float64 on ``device`` and returned as complex64 rows [n_tmpl, ld]
-    (ld >= n/2+1; columns past n/2 are zero).  Used to fill multi-GB banks
-    without a host round trip; numerically it matches ``taylorf2`` to float64
-    rounding before the final cast."""
+    (ld >= n/2+1; columns outside each template's band are zero).  Used to fill
+    multi-GB banks without a host round trip; numerically it matches
+    ``taylorf2`` to float64 rounding before the final cast.  Templates are
+    evaluated ``block`` at a time on the union of their bands."""
     import torch
 
     m1 = np.atleast_1d(np.asarray(m1, dtype=np.float64))
@@ -206,25 +207,35 @@ def taylorf2_torch(n, fs, m1, m2, f_low, device, out=None, ld=None):
         out = torch.zeros((nt, ld), dtype=torch.complex64, device=device)
     else:
         out.zero_()
-    f = torch.arange(nb, dtype=torch.float64, device=device) * (fs / n)
     lv_lso = math.log(1.0 / math.sqrt(6.0))
-    for i in range(nt):
-        M = (m1[i] + m2[i]) * MTSUN_S
-        eta = m1[i] * m2[i] / (m1[i] + m2[i]) ** 2
-        p, log5, log6 = _pn_phase_coeffs(eta)
-        fhi = min(float(f_isco(m1[i], m2[i])), fs / 2.0)
-        k0 = int(math.ceil(f_low * n / fs - 1e-9))
-        k1 = min(int(math.floor(fhi * n / fs + 1e-9)), n // 2 - 1)
-        if k1 < k0:
+    M = (m1 + m2) * MTSUN_S
+    eta = m1 * m2 / (m1 + m2) ** 2
+    fhi = np.minimum(f_isco(m1, m2), fs / 2.0)
+    k0 = int(math.ceil(f_low * n / fs - 1e-9))
+    k1 = np.minimum(np.floor(fhi * n / fs + 1e-9).astype(np.int64), n // 2 - 1)
+    for b0 in range(0, nt, block):
+        b1 = min(nt, b0 + block)
+        kmax = int(k1[b0:b1].max())
+        if kmax < k0:
             continue
-        ff = f[k0:k1 + 1]
-        v = torch.pow(math.pi * M * ff, 1.0 / 3.0)
+        ff = torch.arange(k0, kmax + 1, dtype=torch.float64, device=device) * (fs / n)
+        coef = np.array([_pn_phase_coeffs(e) for e in eta[b0:b1]], dtype=object)
+        P = torch.tensor(np.array([c[0] for c in coef], dtype=np.float64), device=device)  # [b, 8]
+        L5 = torch.tensor(np.array([c[1] for c in coef], dtype=np.float64), device=device)[:, None]
+        L6 = torch.tensor(np.array([c[2] for c in coef], dtype=np.float64), device=device)[:, None]
+        Mb = torch.tensor(M[b0:b1], dtype=torch.float64, device=device)[:, None]
+        eb = torch.tensor(eta[b0:b1], dtype=torch.float64, device=device)[:, None]
+        v = torch.pow(math.pi * Mb * ff[None, :], 1.0 / 3.0)
         lv = torch.log(v)
-        s = p[0] + v * v * (p[2] + v * (p[3] + v * (p[4] + v * (
-            p[5] + log5 * (lv - lv_lso) + v * (p[6] + log6 * lv + v * p[7])))))
-        ph = -math.pi / 4.0 + 3.0 / (128.0 * eta * v ** 5) * s
-        a = ff ** (-7.0 / 6.0)
-        out[i, k0:k1 + 1] = torch.complex(a * torch.cos(ph), -a * torch.sin(ph)).to(torch.complex64)
+        p = [P[:, i:i + 1] for i in range(8)]
+        sv = p[0] + v * v * (p[2] + v * (p[3] + v * (p[4] + v * (
+            p[5] + L5 * (lv - lv_lso) + v * (p[6] + L6 * lv + v * p[7])))))
+        ph = -math.pi / 4.0 + 3.0 / (128.0 * eb * v ** 5) * sv
+        a = ff[None, :] ** (-7.0 / 6.0)
+        kk = torch.arange(k0, kmax + 1, device=device)[None, :]
+        inband = kk <= torch.tensor(k1[b0:b1], device=device)[:, None]
+        a = torch.where(inband, a, torch.zeros((), dtype=torch.float64, device=device))
+        out[b0:b1, k0:kmax + 1] = torch.complex(a * torch.cos(ph), -a * torch.sin(ph)).to(torch.complex64)
     return out
 
 
