@@ -32,6 +32,12 @@ struct mf_plan_s {
   double* sigmasq_dev = nullptr;
   float* inv_sigma_dev = nullptr;
   int32_t* sel_all = nullptr;
+  // data pre-scaling for the raw-|z|^2 epilogue: q' = w s~ / sigma_ref,
+  // ratio[t] = scale_t sigma_ref / sigma_t, thr_raw[t] = rho_thr^2 / ratio[t]^2
+  double sigma_ref = 1.0;
+  float* ratio_dev = nullptr;
+  float* thr_raw_dev = nullptr;
+  bool scale_valid = false;
   // filter work space
   float2* q = nullptr;
   int64_t ld_q = 0;
@@ -71,6 +77,7 @@ struct mf_plan_s {
   int64_t fz_counters_cap = 0;
   int* status = nullptr;    // device status word
   float2* tw = nullptr;     // sub-FFT twiddle tables [2][1024]
+  float2* tw4 = nullptr;    // four-step twiddles w_N^m, m < 32 * N2
   // instrumentation
   mf_plan_stats stats{};
   bool prof = false;
@@ -153,10 +160,29 @@ void make_weights(const mf_plan_desc& d, const double* psd, std::vector<double>&
 }
 
 mf_status recompute_sigmasq(mf_plan_t p, int64_t row0, int64_t n_rows) {
+  p->scale_valid = false;
   if (!p->psd_set || !p->bank || n_rows <= 0) return MF_OK;
   cudaError_t e = mf::launch_sigmasq(p->bank, bank_type(p->bank_dtype), p->ld_bank, p->scales_dev, row0, n_rows,
                                      p->w_dev, p->nb, p->sigmasq_dev, p->inv_sigma_dev, p->st);
   if (e != cudaSuccess) return cuda_fail(p, e, "sigma^2 kernel");
+  return MF_OK;
+}
+
+// sigma_ref = max_t sigma_t (host copy of the FP64 norms), then ratio / thr_raw on the device
+mf_status refresh_scale(mf_plan_t p) {
+  if (p->scale_valid) return MF_OK;
+  std::vector<double> s2(p->n_tmpl);
+  cudaError_t e = cudaMemcpyAsync(s2.data(), p->sigmasq_dev, p->n_tmpl * sizeof(double), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter sigma^2 readback");
+  double mx = 0.0;
+  for (double v : s2)
+    if (std::isfinite(v) && v > mx) mx = v;
+  p->sigma_ref = mx > 0.0 ? std::sqrt(mx) : 1.0;
+  e = mf::launch_tmpl_scale(p->inv_sigma_dev, p->n_tmpl, p->sigma_ref, p->d.snr_thr * p->d.snr_thr, p->ratio_dev,
+                            p->thr_raw_dev, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter template scales");
+  p->scale_valid = true;
   return MF_OK;
 }
 
@@ -228,7 +254,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   p->ld_q = (p->nb + 63) / 64 * 64;
   // batch of templates per pass pair: keep the pass-1 -> pass-2 scratch within ~64 MB (L2 resident)
   const int64_t per = (int64_t)d.n_det * d.n * (int64_t)sizeof(float2);
-  int64_t budget = int64_t(128) << 20;
+  int64_t budget = int64_t(256) << 20;
   if (const char* b = std::getenv("MF_SCRATCH_MB")) budget = std::max<int64_t>(1, std::atoll(b)) << 20;
   p->batch = (int)std::max<int64_t>(1, std::min<int64_t>(budget / per, 4096));
   if (const char* v = std::getenv("MF_FILTER_IMPL")) p->impl = std::atoi(v);
@@ -245,14 +271,16 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
       (s = dalloc(p, &p->trig, (size_t)d.max_triggers * sizeof(mf_trigger), "triggers")) != MF_OK ||
       (s = dalloc(p, &p->count, sizeof(int64_t), "count")) != MF_OK ||
       (s = dalloc(p, &p->status, sizeof(int), "status")) != MF_OK ||
-      (s = dalloc(p, &p->tw, 2 * 1024 * sizeof(float2), "twiddles")) != MF_OK) {
+      (s = dalloc(p, &p->tw, 2 * 1024 * sizeof(float2), "twiddles")) != MF_OK ||
+      (s = dalloc(p, &p->tw4, (size_t)32 * p->n2 * sizeof(float2), "four-step twiddles")) != MF_OK) {
     g_err = p->err;
     mf_destroy(p);
     return s;
   }
   cudaMemsetAsync(p->count, 0, sizeof(int64_t), p->st);
   cudaMemsetAsync(p->status, 0, sizeof(int), p->st);
-  if (mf::launch_fill_twiddles(d.n, p->tw, p->tw + 1024, p->st) != cudaSuccess) {
+  if (mf::launch_fill_twiddles(d.n, p->tw, p->tw + 1024, p->st) != cudaSuccess ||
+      mf::launch_fill_tw4(d.n, p->tw4, (int64_t)32 * p->n2, p->st) != cudaSuccess) {
     g_err = "mf_plan: twiddle table kernel";
     mf_destroy(p);
     return MF_ECUDA;
@@ -264,10 +292,10 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
 void mf_destroy(mf_plan_t p) {
   if (!p) return;
   if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
-  dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev);
+  dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev); dfree(p->ratio_dev); dfree(p->thr_raw_dev);
   dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
-  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->fz_counters);
+  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4); dfree(p->fz_counters);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
 }
@@ -291,6 +319,7 @@ mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
   cudaStreamSynchronize(p->st);
   p->n_tmpl = 0;
   p->maps_valid = false;
+  p->scale_valid = false;
   p->bank_dtype = dtype;
   p->ld_bank = (p->nb + 63) / 64 * 64;
   const size_t bytes = (size_t)n_tmpl * p->ld_bank * elem_bytes(dtype);
@@ -298,6 +327,8 @@ mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
   if ((s = dalloc(p, &p->bank, bytes, "bank")) != MF_OK ||
       (s = dalloc(p, &p->sigmasq_dev, n_tmpl * sizeof(double), "sigma^2")) != MF_OK ||
       (s = dalloc(p, &p->inv_sigma_dev, n_tmpl * sizeof(float), "1/sigma")) != MF_OK ||
+      (s = dalloc(p, &p->ratio_dev, n_tmpl * sizeof(float), "sigma ratio")) != MF_OK ||
+      (s = dalloc(p, &p->thr_raw_dev, n_tmpl * sizeof(float), "raw thresholds")) != MF_OK ||
       (s = dalloc(p, &p->sel_all, n_tmpl * sizeof(int32_t), "all-template selection")) != MF_OK)
     return s;
   if (dtype != MF_F32) {
@@ -390,6 +421,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   const int64_t n_sel = n_subset < 0 ? p->n_tmpl : n_subset;
   mf_status s = ensure_slots(p, std::max<int64_t>(n_sel, 1));
   if (s != MF_OK) return s;
+  if ((s = refresh_scale(p)) != MF_OK) return s;
   cudaError_t e = cudaSuccess;
   if (n_sel > 0)
     e = cudaMemcpyAsync(p->sel_copy, n_subset < 0 ? p->sel_all : subset, n_sel * sizeof(int32_t), cudaMemcpyDeviceToDevice,
@@ -398,7 +430,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   const int64_t n_slots = (int64_t)p->d.n_det * n_sel * p->n_win;
   const int64_t launches_before = mf::launch_count();
   e = mf::launch_prep((const float2*)dtilde, ld_dtilde, p->w_dev, p->nb, p->d.n_det, p->q, p->ld_q, p->slots, n_slots,
-                      p->st);
+                      p->st, 1.0 / p->sigma_ref);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter prep");
   mf::FilterArgs a{};
   a.n = p->d.n;
@@ -413,7 +445,8 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.q = p->q;
   a.ld_q = p->ld_q;
   a.sel = p->sel_copy;
-  a.inv_sigma = p->inv_sigma_dev;
+  a.inv_sigma = p->ratio_dev;  // 1/sigma on the data scaled by 1/sigma_ref
+  a.thr_raw = p->thr_raw_dev;
   a.scratch = p->scratch;
   const double thr = p->d.snr_thr;
   a.thr2 = (float)(thr * thr);
@@ -426,6 +459,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.status = p->status;
   a.tw1 = p->tw;
   a.tw2 = p->tw + 1024;
+  a.tw4 = p->tw4;
   if (p->impl != 1 && !p->maps_valid) {
     e = mf::filter2_encode_maps(a, p->n_tmpl, &p->maps);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter tensor maps");
@@ -479,6 +513,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   }
   for (int64_t pos0 = 0; p->impl != 3 && pos0 < n_sel; pos0 += p->batch) {
     a.pos0 = pos0;
+    a.first_batch = pos0 == 0 ? 1 : 0;
     a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
     const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
     const int e0 = prof ? (int)p->samples.size() * 3 : 0;

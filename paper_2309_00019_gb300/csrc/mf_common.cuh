@@ -85,4 +85,37 @@ struct FilterEpi {
   }
 };
 
+// Epilogue on raw |z|^2: the data are pre-scaled by 1/sigma_ref, so |z'|^2 is in
+// range, and each template carries thr_raw = rho_thr^2 / ratio^2 and ratio =
+// scale * sigma_ref / sigma (rho = |z'| ratio).  Two instructions and a
+// compare per sample; rho^2 and the phase only for samples over threshold.
+struct RawEpi {
+  const int32_t* sel;
+  const float* ratio;
+  const float* thr_raw;
+  int64_t pos0;
+  int n_det;
+  int64_t window, vb, ve, n_win, n_sel_total;
+  unsigned long long* slots;
+  struct Ser {
+    float ratio, thr;
+    unsigned long long* slot;
+  };
+  __device__ __forceinline__ Ser series(int s) const {
+    const int d = s % n_det;
+    const int64_t pos = pos0 + s / n_det;
+    const int t = sel[pos];
+    return Ser{__ldg(ratio + t), __ldg(thr_raw + t), slots + ((int64_t)d * n_sel_total + pos) * n_win};
+  }
+  __device__ __forceinline__ void operator()(const Ser& se, int64_t n, float2 z) const {
+    const float m2 = fmaf(z.x, z.x, z.y * z.y);
+    if (m2 >= se.thr) {
+      if (n >= vb && n < ve) {
+        const float a = z.x * se.ratio, b = z.y * se.ratio;
+        record_peak(se.slot, n, window, a, b, fmaf(a, a, b * b));
+      }
+    }
+  }
+};
+
 }  // namespace mf

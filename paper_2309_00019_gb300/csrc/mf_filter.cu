@@ -26,16 +26,19 @@ constexpr int kT2 = 128;  // threads per CTA
 
 constexpr int round128(int x) { return (x + 127) / 128 * 128; }
 
+// generic-proxy writes of another grid -> async-proxy (TMA) reads of this one
+__device__ __forceinline__ void fence_proxy_async_global_fwd() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 // Exchange-buffer layout of G groups (columns or rows) of M complex values.
 // For RA >= 16 the buffer is unpadded and XOR-swizzled: logical element i of
 // group c lives at c M + (i & ~15) + ((i & 15) ^ ((i / RA + K c) & 15)), so
 // that the pass-a writes (i = t RA + a) and the pass-b reads (i = j + r RA) of
 // every half-warp touch 16 distinct 8-byte bank pairs; K = lanes a group
 // contributes to a half-warp.  For RA = 8 (M = 64) rows are padded instead.
-template <int M, int K>
+template <int M, int K, bool SWIZZLE = true>
 struct Xch {
   using G = SubFft<M>;
-  static constexpr bool SWZ = G::RA >= 16;
+  static constexpr bool SWZ = SWIZZLE && G::RA >= 16;
   static constexpr int S = SWZ ? M : stride_for(G::PAD, K);
   __device__ __forceinline__ static int idx(int c, int i) {
     if constexpr (SWZ) {
@@ -61,7 +64,7 @@ struct ColGeo {
   static constexpr int H_BYTES = ROWS * C * HB;
   static constexpr int Q_BYTES = ROWS * C * 8;
   static constexpr int K = C >= 16 ? 1 : 16 / C;
-  using X = Xch<N1, K>;
+  using X = Xch<N1, K, false>;
   static constexpr int XCH_BYTES = C * X::S * 8;
   static constexpr int SLOT = round128(H_BYTES + Q_BYTES > XCH_BYTES ? H_BYTES + Q_BYTES : XCH_BYTES);
   static constexpr int TW_BYTES = G::RB * G::RA * 8;
@@ -76,7 +79,7 @@ struct RowGeo {
   static constexpr int RW = kT2 / G::T;                   // rows per item
   static constexpr int ITEM = RW * N2;                    // complex values per item
   static constexpr int K = G::T >= 16 ? 0 : G::T;
-  using X = Xch<N2, K == 0 ? 16 : K>;
+  using X = Xch<N2, K == 0 ? 16 : K, false>;
   static constexpr int XCH_BYTES = RW * X::S * 8;
   static constexpr int SLOT = round128(ITEM * 8 > XCH_BYTES ? ITEM * 8 : XCH_BYTES);
   static constexpr int TW_BYTES = G::RB * G::RA * 8;
@@ -125,11 +128,11 @@ __global__ void __launch_bounds__(kT2, 3)
     k_cols(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUtensorMap tm_q, FilterArgs a) {
   using G = SubFft<N1>;
   using P = ColGeo<N1, BT>;
+  using X = typename P::X;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C;
   constexpr int NCB = N2 / C;
   constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ int ok;
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: slots, [2]: twiddles
   const int tid = threadIdx.x;
@@ -156,21 +159,22 @@ __global__ void __launch_bounds__(kT2, 3)
       tma_load_3d(dst + P::H_BYTES + bx * P::BOXR * C * 8, &tm_q, cb * C, bx * P::BOXR, d, bar + slot);
     }
   };
+  pdl_launch_dependents();  // the next kernel may start its prologue as our CTAs retire
   if (tid == 0) {
     mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
     bulk_g2s(sm + P::TW_OFF, a.tw1, (uint32_t)P::TW_BYTES, bar + 2);
+    // the weighted data come from the kernel just before only for the first batch; otherwise
+    // the first tiles (bank and data, both unchanged) load while the previous kernel drains
+    if (a.first_batch) pdl_wait();
     if ((int)blockIdx.x < n_items) issue(blockIdx.x, 0);
   }
-  if (!cta_wait(bar + 2, 0, a.status, &ok)) return;
+  pdl_wait();  // the previous kernel (reader of the scratch we are about to write) has completed
+  if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) return;
   int k = 0;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
-    __syncthreads();  // the other slot's previous item is completely done
-    if (tid == 0 && item + (int)gridDim.x < n_items) {
-      fence_proxy_async();
-      issue(item + gridDim.x, slot ^ 1);
-    }
-    if (!cta_wait(bar + slot, (uint32_t)((k >> 1) & 1), a.status, &ok)) return;
+    // every thread waits (bounded) for this item's tiles, reads its inputs, then one barrier
+    const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
     const unsigned char* sh = sm + slot * P::SLOT;
     const float2* sq = reinterpret_cast<const float2*>(sh + P::H_BYTES);
     const int s = item / NCB;
@@ -185,10 +189,14 @@ __global__ void __launch_bounds__(kT2, 3)
         v[r] = cmulc(sq[idx], smem_h<BT>(sh, idx));
       }
     }
-    __syncthreads();  // tiles consumed: the slot becomes the exchange buffer
+    // tiles consumed by every thread; the previous item (other slot) is finished too
+    if (__syncthreads_or(fail)) return;
+    if (tid == 0 && item + (int)gridDim.x < n_items) {
+      fence_proxy_async();
+      issue(item + gridDim.x, slot ^ 1);
+    }
     dft<RA, true>(v);
     float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT);
-    using X = typename P::X;
 #pragma unroll
     for (int q = 0; q < RA; ++q) xb[X::idx(c, t * RA + q)] = v[q];
     __syncthreads();
@@ -201,8 +209,9 @@ __global__ void __launch_bounds__(kT2, 3)
 #pragma unroll
       for (int r = 1; r < RB; ++r) u[r] = cmul(xb[X::idx(c, j + r * RA)], tw[r * RA + j]);
       dft<RB>(u);
-      float2 w = unit_root(((uint32_t)j * (uint32_t)k2) & (N - 1), N);
-      const float2 st = unit_root(((uint32_t)RA * (uint32_t)k2) & (N - 1), N);
+      // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q, both from the table
+      float2 w = __ldg(a.tw4 + (uint32_t)j * (uint32_t)k2);
+      const float2 st = __ldg(a.tw4 + (uint32_t)RA * (uint32_t)k2);
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
         st_global_hint(out + (int64_t)(j + q * RA) * N2 + k2, cmul(u[q], w), pol_keep);
@@ -220,11 +229,11 @@ template <int N1, int N2>
 __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
   using G = SubFft<N2>;
   using P = RowGeo<N2>;
+  using X = typename P::X;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW;
   constexpr int NRB = N1 / RW;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ int ok;
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);
   const int tid = threadIdx.x;
@@ -244,33 +253,34 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
     bulk_g2s_hint(sm + slot * P::SLOT, a.scratch + (int64_t)s * N + (int64_t)j10 * N2, (uint32_t)(P::ITEM * 8),
                   bar + slot, pol_last_use);
   };
+  pdl_launch_dependents();
   if (tid == 0) {
     mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
     bulk_g2s(sm + P::TW_OFF, a.tw2, (uint32_t)P::TW_BYTES, bar + 2);
+    pdl_wait();  // the scratch is written by the kernel just before
+    fence_proxy_async_global_fwd();
     if ((int)blockIdx.x < n_items) issue(blockIdx.x, 0);
   }
-  if (!cta_wait(bar + 2, 0, a.status, &ok)) return;
-  FilterEpi ep{a.sel, a.inv_sigma, a.pos0, a.n_det, a.thr2, a.window, a.valid_begin, a.valid_end,
-               a.n_win, a.n_sel_total, a.slots};
+  if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) return;
+  RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, a.pos0, a.n_det, a.window, a.valid_begin, a.valid_end,
+            a.n_win, a.n_sel_total, a.slots};
   int k = 0;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
-    __syncthreads();
-    if (tid == 0 && item + (int)gridDim.x < n_items) {
-      fence_proxy_async();
-      issue(item + gridDim.x, slot ^ 1);
-    }
-    if (!cta_wait(bar + slot, (uint32_t)((k >> 1) & 1), a.status, &ok)) return;
+    const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
     const float2* stage = reinterpret_cast<const float2*>(sm + slot * P::SLOT);
     const int s = item / NRB;
     const int j1 = (item % NRB) * RW + row;
     float2 v[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r) v[r] = stage[row * N2 + t + r * RB];
-    __syncthreads();
+    if (__syncthreads_or(fail)) return;
+    if (tid == 0 && item + (int)gridDim.x < n_items) {
+      fence_proxy_async();
+      issue(item + gridDim.x, slot ^ 1);
+    }
     dft<RA>(v);
     float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT);
-    using X = typename P::X;
 #pragma unroll
     for (int q = 0; q < RA; ++q) xb[X::idx(row, t * RA + q)] = v[q];
     __syncthreads();
@@ -701,6 +711,22 @@ int sm_count() {
   return n;
 }
 
+// launch with programmatic stream serialization (overlaps our prologue with the previous kernel's tail)
+template <class K, class... Args>
+cudaError_t launch_pdl(K kern, int grid, int smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kT2);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 int grid2(int items) {
   const int g = sm_count() * 3;
   return items < g ? items : g;
@@ -717,9 +743,9 @@ cudaError_t run_cols(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st)
     attr = true;
   }
   const int items = a.count * a.n_det * (N2 / P::C);
-  k<<<grid2(items), kT2, P::SMEM, st>>>(m.h, m.q, a);
+  cudaError_t e = launch_pdl(k, grid2(items), P::SMEM, st, m.h, m.q, a);
   add_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 template <int N1, int N2>
@@ -743,9 +769,9 @@ cudaError_t run_rows(const FilterArgs& a, cudaStream_t st) {
     attr = true;
   }
   const int items = a.count * a.n_det * (N1 / P::RW);
-  k<<<grid2(items), kT2, P::SMEM, st>>>(a);
+  cudaError_t e = launch_pdl(k, grid2(items), P::SMEM, st, a);
   add_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 #define MF_DISPATCH2(n, FN, ARGS)            \
@@ -962,6 +988,19 @@ cudaError_t run_fill_tw(float2* tw1, float2* tw2, cudaStream_t st) {
   return cudaGetLastError();
 }
 }  // namespace
+
+namespace {
+__global__ void k_fill_tw4(float2* tw4, int64_t count, uint32_t n) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < count; m += (int64_t)gridDim.x * blockDim.x)
+    tw4[m] = unit_root((uint32_t)m, n);
+}
+}  // namespace
+
+cudaError_t launch_fill_tw4(int64_t n, float2* tw4, int64_t count, cudaStream_t st) {
+  k_fill_tw4<<<64, 256, 0, st>>>(tw4, count, (uint32_t)n);
+  add_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st) {
   MF_DISPATCH2(n, run_fill_tw, (tw1, tw2, st))

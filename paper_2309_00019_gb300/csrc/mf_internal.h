@@ -48,6 +48,9 @@ struct FilterArgs {
   int* status;              // device status word (bounded waits report here)
   const float2* tw1;        // sub-FFT twiddle tables (w_N1^{r j}, w_N2^{r j}), 8 KB max each
   const float2* tw2;
+  const float* thr_raw;     // per template: rho_thr^2 / ratio^2 on the pre-scaled data (TMA kernels)
+  const float2* tw4;        // four-step twiddles w_N^m, m < RA(N1) * N2 (TMA kernels)
+  int first_batch;          // 1: the weighted data were written by the kernel just before (PDL ordering)
 };
 
 // Tensor maps of the TMA-staged filter: template bank and weighted data, each
@@ -64,6 +67,8 @@ cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter4_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter4_pass2(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st);
+// w_N^m for m < count (count <= 32768)
+cudaError_t launch_fill_tw4(int64_t n, float2* tw4, int64_t count, cudaStream_t st);
 
 // Schedule of the fused persistent filter (both passes of every batch in one
 // launch).  The selection is cut into nb batches of B templates (the last one
@@ -92,7 +97,10 @@ void add_launches(int64_t n);
 
 cudaError_t launch_prep(const float2* dtilde, int64_t ld_d, const double* w, int64_t nb, int n_det,
                         float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots,
-                        cudaStream_t st);
+                        cudaStream_t st, double q_scale = 1.0);
+// ratio[t] = inv_sigma[t] * sigma_ref, thr_raw[t] = thr2 / ratio[t]^2 (+inf when ratio is 0)
+cudaError_t launch_tmpl_scale(const float* inv_sigma, int64_t n_tmpl, double sigma_ref, double thr2, float* ratio,
+                              float* thr_raw, cudaStream_t st);
 cudaError_t launch_filter_batch(const FilterArgs& a, cudaStream_t st);
 // the two halves of launch_filter_batch, for per-kernel timing
 cudaError_t launch_filter_pass1(const FilterArgs& a, cudaStream_t st);

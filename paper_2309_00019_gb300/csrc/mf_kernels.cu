@@ -308,14 +308,23 @@ cudaError_t run_rfft(const float* x, int64_t ld_s, int n_det, double dt, float2*
 // ---------------------------------------------------------------------------
 
 __global__ void k_prep(const float2* __restrict__ d, int64_t ld_d, const double* __restrict__ w, int64_t nb,
-                       int n_det, float2* __restrict__ q, int64_t ld_q) {
+                       int n_det, float2* __restrict__ q, int64_t ld_q, double q_scale) {
   const int64_t total = nb * n_det;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int det = (int)(i / nb);
     const int64_t k = i - (int64_t)det * nb;
-    const double wk = w[k];
+    const double wk = w[k] * q_scale;
     const float2 s = d[(int64_t)det * ld_d + k];
     q[(int64_t)det * ld_q + k] = make_float2((float)(wk * (double)s.x), (float)(wk * (double)s.y));
+  }
+}
+
+__global__ void k_tmpl_scale(const float* __restrict__ inv_sigma, int64_t n, double sigma_ref, double thr2,
+                             float* __restrict__ ratio, float* __restrict__ thr_raw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = (double)inv_sigma[i] * sigma_ref;
+    ratio[i] = (float)r;
+    thr_raw[i] = r > 0.0 ? (float)(thr2 / (r * r)) : __int_as_float(0x7f800000);
   }
 }
 
@@ -481,10 +490,19 @@ __global__ void k_compact_write(const unsigned long long* __restrict__ slots, in
 // launchers
 // ---------------------------------------------------------------------------
 
+cudaError_t launch_tmpl_scale(const float* inv_sigma, int64_t n_tmpl, double sigma_ref, double thr2, float* ratio,
+                              float* thr_raw, cudaStream_t st) {
+  if (n_tmpl <= 0) return cudaSuccess;
+  k_tmpl_scale<<<num_sms() * 2, 256, 0, st>>>(inv_sigma, n_tmpl, sigma_ref, thr2, ratio, thr_raw);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const float2* dtilde, int64_t ld_d, const double* w, int64_t nb, int n_det,
-                        float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st) {
+                        float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st,
+                        double q_scale) {
   const int g = num_sms() * 4;
-  k_prep<<<g, 256, 0, st>>>(dtilde, ld_d, w, nb, n_det, q, ld_q);
+  k_prep<<<g, 256, 0, st>>>(dtilde, ld_d, w, nb, n_det, q, ld_q, q_scale);
   ++g_launches;
   if (slots && n_slots > 0) {
     k_zero_u64<<<g, 256, 0, st>>>(slots, n_slots);
