@@ -216,6 +216,50 @@ mf_status mf_set_nbhd(mf_plan_t plan, const int64_t* ptr, const int32_t* idx, in
  * [n_tmpl of this plan]; *n_subset (host) receives the count.  Synchronises. */
 mf_status mf_nbhd_union(mf_plan_t plan, const int32_t* followed, int32_t* subset, int64_t* n_subset);
 
+/* ---- learned proposal for the stage-2 follow-up ------------------------- */
+
+/* Sec. III filters every fine template in the neighbourhood of a followed-up
+ * coarse template.  This network (not in the paper; a ranking aid with the
+ * full neighbourhood as the fallback) scores the n_valid[i] neighbourhood
+ * slots of candidate i so that stage 2 can filter only the best-ranked
+ * ones.  Architecture: x [n_in] -> depth x (affine + GELU, width) -> affine
+ * [n_out] -> softmax over the first n_valid slots.  Parameters: FP32 master
+ * copy, flat layout W_1 [n_in][width], b_1, ..., W_depth, b_depth,
+ * W_out [width][n_out], b_out (row-major); products in BF16 on the tensor
+ * cores with FP32 accumulation.  All arrays are device pointers unless
+ * stated; calls are asynchronous on the network's stream except
+ * set/get_params, which synchronise. */
+typedef struct mf_mlp_s* mf_mlp_t;
+
+/* Create a network with zero parameters for batches of up to max_batch rows.
+ * Errors: MF_EINVAL (sizes), MF_ENOMEM. */
+mf_status mf_mlp_create(mf_mlp_t* out, int32_t n_in, int32_t width, int32_t depth, int32_t n_out, int64_t max_batch,
+                        void* cuda_stream);
+void mf_mlp_destroy(mf_mlp_t net);
+/* Number of FP32 parameters (layout above). */
+int64_t mf_mlp_num_params(mf_mlp_t net);
+/* Copy parameters in (host or device per on_device; resets the AdamW state) / out (to host). */
+mf_status mf_mlp_set_params(mf_mlp_t net, const float* theta, int64_t n, int on_device);
+mf_status mf_mlp_get_params(mf_mlp_t net, float* theta, int64_t n);
+/* Forward pass of x [B][n_in] (FP32); logits [B][n_out] (FP32) if non-NULL. */
+mf_status mf_mlp_forward(mf_mlp_t net, const float* x, int64_t B, float* logits);
+/* Forward + backward of the mean masked softmax cross-entropy with labels
+ * label[B] in [0, n_valid[i]); writes loss (1 float) and the gradient
+ * (n_params floats) when those pointers are non-NULL; keeps the gradient for
+ * mf_mlp_adamw_step. */
+mf_status mf_mlp_loss_grad(mf_mlp_t net, const float* x, const int32_t* n_valid, const int32_t* label, int64_t B,
+                           float* loss, float* grad);
+/* One AdamW step (decoupled weight decay on every parameter) with the last gradient. */
+mf_status mf_mlp_adamw_step(mf_mlp_t net, float lr, float beta1, float beta2, float eps, float weight_decay);
+/* Proposal: the best-scored valid slots of each row in order (ties: lower
+ * slot), until their softmax probability over the valid slots reaches p_mass
+ * (p_mass >= 1: exactly min(k, n_valid) slots) or k (<= 64) are taken;
+ * out [B][k] int32, -1 padded; count [B] int32 (may be NULL) = slots taken. */
+mf_status mf_mlp_topk(mf_mlp_t net, const float* x, const int32_t* n_valid, int64_t B, int32_t k, float p_mass,
+                      int32_t* out, int32_t* count);
+/* Message of the last failed call on this network. */
+const char* mf_mlp_last_error(mf_mlp_t net);
+
 /* ---- filtering without device allocation ------------------------------- */
 
 /* The filter of mf_filter (same arithmetic, threshold, window maxima and

@@ -137,3 +137,27 @@ def topk_valid(logits, n_valid, k):
         order = sorted(range(nv), key=lambda j: (-logits[i, j], j))[:k]
         out[i, :len(order)] = order
     return out
+
+
+def propose_mass(logits, n_valid, k, p_mass):
+    """The proposal rule on top of the ranking: valid slots in decreasing
+    logit order (ties: lower slot first), taken until their softmax
+    probability over the valid slots reaches p_mass, or k slots are taken;
+    rows padded with -1.  p_mass >= 1 gives topk_valid."""
+    B, n_out = logits.shape
+    out = np.full((B, k), -1, dtype=np.int64)
+    for i in range(B):
+        nv = int(n_valid[i])
+        if nv <= 0:
+            continue
+        l = np.asarray(logits[i, :nv], np.float64)
+        p = np.exp(l - l.max())
+        p /= p.sum()
+        order = sorted(range(nv), key=lambda j: (-l[j], j))
+        cum = 0.0
+        for r, j in enumerate(order[:k]):
+            out[i, r] = j
+            cum += p[j]
+            if cum >= p_mass:
+                break
+    return out

@@ -80,6 +80,16 @@ SIGNATURES = {
     "mf_set_nbhd": (C.c_int, [_P, _P, _P, _I64, C.c_int]),
     "mf_nbhd_union": (C.c_int, [_P, _P, _P, C.POINTER(_I64)]),
     "mf_profile": (C.c_int, [_P, C.c_int]),
+    "mf_mlp_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.c_int32, C.c_int32, _I64, _P]),
+    "mf_mlp_destroy": (None, [_P]),
+    "mf_mlp_num_params": (_I64, [_P]),
+    "mf_mlp_set_params": (C.c_int, [_P, _P, _I64, C.c_int]),
+    "mf_mlp_get_params": (C.c_int, [_P, _P, _I64]),
+    "mf_mlp_forward": (C.c_int, [_P, _P, _I64, _P]),
+    "mf_mlp_loss_grad": (C.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "mf_mlp_adamw_step": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "mf_mlp_topk": (C.c_int, [_P, _P, _P, _I64, C.c_int32, C.c_float, _P, _P]),
+    "mf_mlp_last_error": (C.c_char_p, [_P]),
     "mf_filter_noalloc": (C.c_int, [C.c_double, _I64, C.c_int32, C.c_double, C.c_double, C.c_double, _I64, _P, _P,
                                     _I64, _I64, _P, _I64, _P, _I64, _P, _P]),
     "mf_get_stats": (C.c_int, [_P, C.POINTER(mf_plan_stats), C.c_int]),
@@ -257,3 +267,57 @@ class Plan:
         st = mf_plan_stats()
         _check(self.h, self.lib.mf_get_stats(self.h, C.byref(st), int(reset)))
         return {f: getattr(st, f) for f, _ in mf_plan_stats._fields_}
+
+
+class MLP:
+    """Owner of one ``mf_mlp_t`` (learned proposal network); methods mirror the C calls."""
+
+    def __init__(self, n_in, width, depth, n_out, max_batch, stream=None):
+        lib = load()
+        h = _P()
+        _check(None, lib.mf_mlp_create(C.byref(h), n_in, width, depth, n_out, max_batch, stream))
+        self.h, self.lib = h, lib
+        self.dims = (n_in, width, depth, n_out)
+        self.n_params = lib.mf_mlp_num_params(h)
+
+    def _chk(self, st):
+        if st != MF_OK:
+            msg = self.lib.mf_mlp_last_error(self.h)
+            raise MFError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        if isinstance(theta, np.ndarray):
+            t = np.ascontiguousarray(theta, dtype=np.float32)
+            self._chk(self.lib.mf_mlp_set_params(self.h, t.ctypes.data, len(t), 0))
+        else:
+            self._chk(self.lib.mf_mlp_set_params(self.h, _ptr(theta), theta.numel(), 1))
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._chk(self.lib.mf_mlp_get_params(self.h, out.ctypes.data, self.n_params))
+        return out
+
+    def forward(self, x, logits=None):
+        self._chk(self.lib.mf_mlp_forward(self.h, _ptr(x), x.shape[0], _ptr(logits)))
+
+    def loss_grad(self, x, n_valid, label, loss=None, grad=None):
+        self._chk(self.lib.mf_mlp_loss_grad(self.h, _ptr(x), _ptr(n_valid), _ptr(label), x.shape[0], _ptr(loss),
+                                            _ptr(grad)))
+
+    def adamw_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        self._chk(self.lib.mf_mlp_adamw_step(self.h, lr, beta1, beta2, eps, weight_decay))
+
+    def topk(self, x, n_valid, k, out, p_mass=2.0, count=None):
+        self._chk(self.lib.mf_mlp_topk(self.h, _ptr(x), _ptr(n_valid), x.shape[0], k, p_mass, _ptr(out),
+                                       _ptr(count)))

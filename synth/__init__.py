@@ -38,4 +38,5 @@ from .configs import (  # noqa: F401
     make_config1,
     Config2,
     make_config2,
+    make_banks,
 )

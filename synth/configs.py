@@ -100,6 +100,20 @@ class Config2:
                                     dtype=dtype) for i in ids])
 
 
+def _banks(rng, n_coarse, n_fine, f_low, f_high, min_match):
+    cm1, cm2, _, _ = g.sample_bank_chirp_times(rng, n_coarse, f_low)
+    fm1, fm2, _, _ = g.sample_bank_chirp_times(rng, n_fine, f_low)
+    ptr, idx, val = g.nbhd_map(cm1, cm2, fm1, fm2, f_low, f_low, f_high, min_match=min_match)
+    return cm1, cm2, fm1, fm2, ptr, idx, val
+
+
+def make_banks(seed=1, n_coarse=2000, n_fine=20000, f_low=30.0, f_high=1024.0, min_match=0.9):
+    """The coarse and fine banks and neighbourhood map of the two-stage workload
+    alone (the same draws as make_config2 with the same seed):
+    (coarse m1, m2, fine m1, m2, nbhd ptr, nbhd idx, nbhd match)."""
+    return _banks(np.random.default_rng(seed), n_coarse, n_fine, f_low, f_high, min_match)
+
+
 def make_config2(seed=1, small=False):
     if small:
         T, n_coarse, n_fine, n_glitch, n_inj, n_shifts, min_match = 32.0, 48, 480, 4, 4, 5, 0.5
@@ -110,9 +124,7 @@ def make_config2(seed=1, small=False):
     n1 = int(T * fs1)
     rng = np.random.default_rng(seed)
     # banks: random in the chirp-time plane, chirp mass 1.2-10
-    cm1, cm2, _, _ = g.sample_bank_chirp_times(rng, n_coarse, f_low)
-    fm1, fm2, _, _ = g.sample_bank_chirp_times(rng, n_fine, f_low)
-    ptr, idx, val = g.nbhd_map(cm1, cm2, fm1, fm2, f_low, f_low, fs2 / 2, min_match=min_match)
+    cm1, cm2, fm1, fm2, ptr, idx, val = _banks(rng, n_coarse, n_fine, f_low, fs2 / 2, min_match)
     # noise
     nb = n2 // 2 + 1
     fd = np.stack([g.coloured_noise_fd(rng, n2, fs2) for _ in range(2)])

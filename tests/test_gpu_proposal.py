@@ -1,0 +1,172 @@
+"""GPU checks of the learned proposal: the network kernels against the FP64
+oracle (forward logits, loss and gradient, AdamW step, top-k), and what the
+trained network gains over the plain neighbourhood follow-up on candidates
+the pipeline generates itself."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp_oracle as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mfmod(lib):
+    from paper_2309_00019_gb300 import mf
+    return mf
+
+
+def _batch(rng, B, n_in, n_out):
+    x = rng.standard_normal((B, n_in)).astype(np.float32)
+    nv = rng.integers(1, min(n_out, 40) + 1, B).astype(np.int32)
+    nv[0] = n_out  # one row with every slot valid
+    lab = np.array([rng.integers(0, v) for v in nv], np.int32)
+    return x, nv, lab
+
+
+@pytest.mark.parametrize("dims", [(5, 16, 2, 12), (5, 256, 4, 2000)])
+def test_forward_loss_gradient_match_fp64_oracle(mfmod, dims):
+    rng = np.random.default_rng(1)
+    net = mfmod.MLP(*dims, max_batch=64)
+    theta = M.init_params(rng, dims).astype(np.float32)
+    net.set_params(theta)
+    x, nv, lab = _batch(rng, 64, dims[0], dims[3])
+    xd = torch.from_numpy(x).to(DEV)
+    logits = torch.zeros((64, dims[3]), dtype=torch.float32, device=DEV)
+    net.forward(xd, logits)
+    ref, _ = M.forward(theta.astype(np.float64), x, dims)
+    got = logits.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+    loss = torch.zeros(1, device=DEV)
+    grad = torch.zeros(net.n_params, device=DEV)
+    net.loss_grad(xd, torch.from_numpy(nv).to(DEV), torch.from_numpy(lab).to(DEV), loss, grad)
+    rl, rg = M.loss_and_grad(theta.astype(np.float64), x, nv, lab, dims)
+    assert float(loss.item()) == pytest.approx(rl, rel=2e-2)
+    g = grad.cpu().numpy().astype(np.float64)
+    # BF16 products: gradient agrees to ~1e-2 in norm and direction
+    assert np.linalg.norm(g - rg) <= 3e-2 * np.linalg.norm(rg)
+    assert g @ rg / (np.linalg.norm(g) * np.linalg.norm(rg)) > 0.999
+    # per layer block (weights of the first layer see the BF16-rounded inputs)
+    off = 0
+    for a, b in M.layer_shapes(*dims):
+        blk = slice(off, off + a * b + b)
+        off += a * b + b
+        assert np.linalg.norm(g[blk] - rg[blk]) <= 5e-2 * np.linalg.norm(rg[blk]) + 1e-7
+
+
+def test_adamw_step_matches_oracle(mfmod):
+    dims = (5, 16, 2, 12)
+    rng = np.random.default_rng(2)
+    net = mfmod.MLP(*dims, max_batch=32)
+    theta = M.init_params(rng, dims).astype(np.float32)
+    net.set_params(theta)
+    x, nv, lab = _batch(rng, 32, dims[0], dims[3])
+    grad = torch.zeros(net.n_params, device=DEV)
+    net.loss_grad(torch.from_numpy(x).to(DEV), torch.from_numpy(nv).to(DEV), torch.from_numpy(lab).to(DEV),
+                  None, grad)
+    g = grad.cpu().numpy().astype(np.float64)
+    net.adamw_step(1e-2, 0.9, 0.999, 1e-8, 1e-3)
+    th_gpu = net.get_params().astype(np.float64)
+    th_ref, _, _ = M.adamw(theta.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-2, 0.9, 0.999,
+                           1e-8, 1e-3)
+    assert np.allclose(th_gpu, th_ref, rtol=1e-5, atol=1e-6)
+
+
+def test_topk_matches_oracle_ranking(mfmod):
+    dims = (5, 32, 2, 50)
+    rng = np.random.default_rng(3)
+    net = mfmod.MLP(*dims, max_batch=128)
+    theta = M.init_params(rng, dims).astype(np.float32)
+    net.set_params(theta)
+    x, nv, _ = _batch(rng, 128, dims[0], dims[3])
+    out = torch.zeros((128, 4), dtype=torch.int32, device=DEV)
+    net.topk(torch.from_numpy(x).to(DEV), torch.from_numpy(nv).to(DEV), 4, out)  # p_mass 2: plain top-k
+    got = out.cpu().numpy()
+    ref_logits, _ = M.forward(theta.astype(np.float64), x, dims)
+    ref = M.topk_valid(ref_logits, nv, 4)
+    for i in range(128):
+        assert (got[i] >= 0).sum() == min(4, nv[i])
+        assert all(0 <= s < nv[i] for s in got[i] if s >= 0)
+        # same set unless two oracle logits are within BF16 rounding of each other
+        if set(got[i]) != set(ref[i]):
+            l = ref_logits[i]
+            kth = np.sort(l[:nv[i]])[::-1][min(4, nv[i]) - 1]
+            diff = [s for s in set(got[i]) ^ set(ref[i]) if s >= 0]
+            assert all(abs(l[s] - kth) <= 3e-2 * (1 + abs(kth)) for s in diff)
+
+
+def test_learned_proposal_filters_fewer_templates_at_small_snr_loss(mfmod):
+    from paper_2309_00019_gb300.proposal import Proposal, generate_pairs, recovered
+
+    cm1, cm2, fm1, fm2, ptr, idx, _ = synth.make_banks(seed=1)
+    pairs = generate_pairs(17408, cm1, cm2, fm1, fm2, ptr, idx, seed=5)
+    n_tr = len(pairs.x) - 1024
+    tr = type(pairs)(*(getattr(pairs, f)[:n_tr] for f in ("x", "n_valid", "label", "slot_snr", "coarse")))
+    te = type(pairs)(*(getattr(pairs, f)[n_tr:] for f in ("x", "n_valid", "label", "slot_snr", "coarse")))
+    prop = Proposal(max_batch=1024)
+    prop.init(seed=0)
+    hist = prop.fit(tr, epochs=40, lr=2e-3, batch=512)
+    assert hist[-1] < hist[0]
+    mean_nb = float(te.n_valid.mean())
+    report = {}
+    for name, k, pm in (("top1", 1, 2.0), ("top2", 2, 2.0), ("top3", 3, 2.0), ("p90", 64, 0.9),
+                        ("p95", 64, 0.95), ("p99", 64, 0.99)):
+        top = prop.rank(te.x, te.n_valid, k, p_mass=pm)
+        frac, used = recovered(te.slot_snr, te.n_valid, top)
+        report[name] = (float(frac.mean()), float(used.mean()), float((frac >= 0.99).mean()))
+    base = {}
+    for k in (1, 2, 3):
+        b = np.array([list(range(min(k, v))) + [-1] * (k - min(k, v)) for v in te.n_valid])
+        bfrac, bused = recovered(te.slot_snr, te.n_valid, b)
+        base[k] = (float(bfrac.mean()), float(bused.mean()))
+    print("\nlearned proposal, 1024 held-out candidates: mean nbhd %.2f" % mean_nb)
+    print("  (mean recovered SNR fraction, mean templates filtered, fraction of candidates within 1%)")
+    for k, v in report.items():
+        print("  learned", k, tuple(round(x, 4) for x in v))
+    for k, v in base.items():
+        print("  match-order top%d" % k, tuple(round(x, 4) for x in v))
+    # the gain over the plain neighbourhood follow-up (every slot, 100% recovered):
+    # at most 1% mean SNR loss while filtering clearly fewer templates
+    best = min((v for v in report.values() if v[0] >= 0.99), key=lambda v: v[1], default=None)
+    assert best is not None, report
+    assert best[1] <= 0.8 * mean_nb, (best, mean_nb)
+
+
+def test_probability_mass_proposal_matches_oracle(mfmod):
+    dims = (5, 32, 2, 50)
+    rng = np.random.default_rng(4)
+    net = mfmod.MLP(*dims, max_batch=256)
+    theta = M.init_params(rng, dims).astype(np.float32)
+    net.set_params(theta)
+    x, nv, _ = _batch(rng, 256, dims[0], dims[3])
+    nv[1] = 0  # an empty neighbourhood
+    out = torch.zeros((256, 8), dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(256, dtype=torch.int32, device=DEV)
+    net.topk(torch.from_numpy(x).to(DEV), torch.from_numpy(nv).to(DEV), 8, out, p_mass=0.6, count=cnt)
+    got, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+    ref_logits, _ = M.forward(theta.astype(np.float64), x, dims)
+    ref = M.propose_mass(ref_logits, nv, 8, 0.6)
+    assert (got[1] == -1).all() and cnt[1] == 0
+    n_same = 0
+    for i in range(256):
+        assert cnt[i] == (got[i] >= 0).sum()
+        assert all(0 <= s < nv[i] for s in got[i] if s >= 0)
+        if (got[i] == ref[i]).all():
+            n_same += 1
+            continue
+        # a different proposal only where BF16 rounding can move the rule's
+        # decision: two logits within rounding, or the mass within 2% of p_mass
+        l = ref_logits[i, :nv[i]]
+        p = np.exp(l - l.max())
+        p /= p.sum()
+        cum = np.cumsum(np.sort(p)[::-1])
+        near_mass = np.abs(cum[:8] - 0.6).min() < 2e-2
+        srt = np.sort(l)[::-1]
+        near_tie = len(srt) > 1 and np.abs(np.diff(srt[:9])).min() < 3e-2 * (1 + np.abs(srt[:9]).max())
+        assert near_mass or near_tie, (i, got[i], ref[i])
+    assert n_same >= 230

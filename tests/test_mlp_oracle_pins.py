@@ -68,3 +68,19 @@ def test_topk_respects_mask_and_ties():
     logits = np.array([[1.0, 3.0, 3.0, 9.0], [5.0, 1.0, 0.0, 0.0]])
     out = M.topk_valid(logits, np.array([3, 1]), 2)
     assert out.tolist() == [[1, 2], [0, -1]]
+
+
+def test_probability_mass_proposal_hand_cases():
+    # logits ln(0.6), ln(0.3), ln(0.1) (plus an invalid slot): probabilities 0.6, 0.3, 0.1
+    logits = np.log(np.array([[0.3, 0.6, 0.1, 50.0]]))
+    nv = np.array([3])
+    assert M.propose_mass(logits, nv, 4, 0.5).tolist() == [[1, -1, -1, -1]]
+    assert M.propose_mass(logits, nv, 4, 0.85).tolist() == [[1, 0, -1, -1]]
+    assert M.propose_mass(logits, nv, 4, 0.95).tolist() == [[1, 0, 2, -1]]
+    assert M.propose_mass(logits, nv, 2, 0.95).tolist() == [[1, 0]]   # k caps it
+    # p_mass >= 1 is the plain top-k; an empty neighbourhood proposes nothing
+    rng = np.random.default_rng(0)
+    l = rng.standard_normal((20, 9))
+    n = rng.integers(0, 10, 20)
+    assert (M.propose_mass(l, n, 4, 2.0) == M.topk_valid(l, n, 4)).all()
+    assert (M.propose_mass(l, np.zeros(20, int), 3, 0.5) == -1).all()
