@@ -39,4 +39,6 @@ from .configs import (  # noqa: F401
     Config2,
     make_config2,
     make_banks,
+    Config4,
+    make_config4,
 )

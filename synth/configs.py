@@ -166,3 +166,65 @@ def make_config2(seed=1, small=False):
                    nbhd_ptr=ptr, nbhd_idx=idx, nbhd_match=val,
                    strain=strain.astype(np.float32), injections=inj,
                    glitches={k: np.asarray(v) for k, v in gl.items()})
+
+
+@dataclass
+class Config4:
+    """Reduced-precision workload: a fine TaylorF2 bank at 4096 Hz on 256 s
+    segments (N = 2^20) of two detectors with injections."""
+    n: int
+    fs: float
+    f_low: float
+    thr: float
+    window: int
+    psd: np.ndarray
+    m1: np.ndarray
+    m2: np.ndarray
+    noise_fd: np.ndarray          # complex128 [2, N/2+1]
+    inj: dict
+
+    def data_fd(self, device, ld=None):
+        """Noise plus injections as a complex64 torch tensor [2, ld] on device
+        (the injections are evaluated there with ``taylorf2_torch``)."""
+        import torch
+
+        nb = self.n // 2 + 1
+        ld = nb if ld is None else ld
+        dev = torch.device(device)
+        out = torch.zeros((2, ld), dtype=torch.complex128, device=dev)
+        out[:, :nb] = torch.from_numpy(self.noise_fd).to(dev)
+        f = torch.arange(nb, dtype=torch.float64, device=dev) * (self.fs / self.n)
+        w = torch.zeros(nb, dtype=torch.float64, device=dev)
+        psd = torch.from_numpy(self.psd).to(dev)
+        band = (f >= self.f_low) & (torch.arange(nb, device=dev) < self.n // 2) & (psd > 0)
+        w[band] = 4.0 * (self.fs / self.n) / psd[band]
+        im1, im2 = self.inj["m1"], self.inj["m2"]
+        for b0 in range(0, len(im1), 16):
+            b1 = min(len(im1), b0 + 16)
+            h = g.taylorf2_torch(self.n, self.fs, im1[b0:b1], im2[b0:b1], self.f_low, dev).to(torch.complex128)
+            sig = torch.sqrt((w[None, :] * (h.real ** 2 + h.imag ** 2)).sum(dim=1))
+            amp = torch.from_numpy(self.inj["snr"][b0:b1]).to(dev) / sig
+            for d in range(2):
+                t0 = torch.from_numpy(self.inj["tc"][b0:b1] + (self.inj["dt_hl"][b0:b1] if d == 1 else 0.0)).to(dev)
+                ph = torch.from_numpy(self.inj["phi"][b0:b1, d]).to(dev)
+                sh = torch.exp(-2j * math.pi * f[None, :] * t0[:, None] + 1j * ph[:, None])
+                out[d, :nb] += (amp[:, None] * h * sh).sum(dim=0)
+        return out.to(torch.complex64)
+
+
+def make_config4(seed=4, n_tmpl=50000, n_inj=200, f_low=30.0):
+    """50,000 fine templates (chirp mass 1.2-10, the banks' chirp-time
+    distribution), 2 detectors x 256 s at 4096 Hz, 200 injections at optimal
+    SNR U(5, 30) spread evenly over the segment (dt_HL within 10 ms)."""
+    fs, T = 4096.0, 256.0
+    n = int(fs * T)
+    rng = np.random.default_rng(seed)
+    m1, m2, _, _ = g.sample_bank_chirp_times(rng, n_tmpl, f_low)
+    noise = np.stack([g.coloured_noise_fd(rng, n, fs) for _ in range(2)])
+    im1, im2, _, _ = g.sample_bank_chirp_times(rng, n_inj, f_low)
+    slot = T / n_inj
+    inj = dict(m1=im1, m2=im2, snr=rng.uniform(5.0, 30.0, n_inj),
+               tc=(np.arange(n_inj) + 0.5) * slot + rng.uniform(-0.25, 0.25, n_inj) * slot,
+               dt_hl=rng.uniform(-0.010, 0.010, n_inj), phi=rng.uniform(0, 2 * math.pi, (n_inj, 2)))
+    return Config4(n=n, fs=fs, f_low=f_low, thr=5.5, window=int(fs), psd=g.psd_bins(n, fs), m1=m1, m2=m2,
+                   noise_fd=noise, inj=inj)
