@@ -168,6 +168,57 @@ def filter_bank(stilde, bank, psd, n, fs, f_low, f_high, thr, window,
 
 
 # ---------------------------------------------------------------------------
+# overlapping segments of long data (Sec. V.C)
+# ---------------------------------------------------------------------------
+
+def segment_plan(n_samples, tmpl_len, seg_len, window):
+    """Overlapping segments of one template-length class (Sec. V.C analyses the
+    data in overlapping segments; the cut is the reading below, the paper
+    gives none).
+
+    Templates last at most tmpl_len samples and are padded to seg_len.  In a
+    segment the circular filter output at local sample j mixes in data from
+    the segment's far end when j < template length, so the analysed part
+    starts at L = tmpl_len rounded up to whole clustering windows.  Segments
+    advance by stride = seg_len - L rounded down to whole windows (so
+    windows never straddle two segments) and segment s analyses local
+    samples [L, min(L + stride, n_samples - s stride)).  Data past the end are
+    zero.  Returns [(start, begin, end)] in local sample units.
+    """
+    L = -(-int(tmpl_len) // window) * window
+    stride = (seg_len - L) // window * window
+    if stride <= 0:
+        raise ValueError("segment too short for the template length")
+    out = []
+    s = 0
+    while s * stride + L < n_samples:
+        start = s * stride
+        out.append((start, L, min(L + stride, n_samples - start)))
+        s += 1
+    return out
+
+
+def segmented_filter(strain, fs, psd, f_low, f_high, bank, seg_len, tmpl_len, thr, window):
+    """Triggers over long data: each overlapping segment of segment_plan is
+    filtered as in filter_bank (Eq. 1-2) with its analysed range; samples are
+    returned in global units.  strain [n_det, n_samples]; bank and psd on the
+    segment's grid (seg_len / 2 + 1 bins)."""
+    strain = np.atleast_2d(np.asarray(strain, dtype=np.float64))
+    n_det, n_samples = strain.shape
+    recs = []
+    for start, b, e in segment_plan(n_samples, tmpl_len, seg_len, window):
+        seg = np.zeros((n_det, seg_len))
+        take = min(seg_len, n_samples - start)
+        seg[:, :take] = strain[:, start:start + take]
+        trig, _ = filter_bank(strain_to_fd(seg, fs), bank, psd, seg_len, fs, f_low, f_high, thr, window,
+                              valid_begin=b, valid_end=e)
+        trig["sample"] += start
+        recs.append(trig)
+    trig = np.concatenate(recs) if recs else np.zeros(0, TRIGGER_DTYPE)
+    return np.sort(trig, order=["det", "tmpl", "sample"])
+
+
+# ---------------------------------------------------------------------------
 # hierarchy glue (Sec. III)
 # ---------------------------------------------------------------------------
 
