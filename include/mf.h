@@ -50,7 +50,7 @@ typedef enum { MF_F32 = 0, MF_F16 = 1, MF_BF16 = 2 } mf_dtype;
 typedef struct {
   double fs;             /* sampling rate, Hz (> 0) */
   int64_t n;             /* N, a power of two in [2^12, 2^20] */
-  int32_t n_det;         /* detectors, 1..8 */
+  int32_t n_det;         /* data rows (detectors, or detector x segment), 1..65536 */
   double f_low, f_high;  /* band edges, Hz */
   mf_dtype dtype;        /* storage type of the template bank */
   double snr_thr;        /* rho threshold (> 0) */
@@ -105,6 +105,40 @@ mf_status mf_bank_reserve(mf_plan_t plan, mf_dtype dtype, int64_t n_tmpl);
  * host float32 [n_rows] or NULL for MF_F32) and compute their sigma^2. */
 mf_status mf_bank_set_rows(mf_plan_t plan, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
                            const float* scales, int on_device);
+
+/* Reduced-precision storage (no counterpart in the paper, which filters in
+ * double precision on CPUs): quantise rows [row0, row0+n_rows) of a 16-bit
+ * bank (reserved as MF_F16 or MF_BF16) from float32 complex templates
+ * htilde [n_rows][ld] (device if on_device, else host).  Each template gets a
+ * power-of-two scale s_t with max |h~_t / s_t| in [2^14, 2^15) (per real and
+ * imaginary component), the stored value is h~_t / s_t rounded to nearest
+ * even, and sigma_t^2 (Eq. 2) is computed in float64 from the stored values
+ * times s_t, so the normalisation matches what is filtered.  Synchronises.
+ * Errors: MF_ESTATE (no bank, or an MF_F32 bank), MF_EINVAL, MF_ENOMEM. */
+mf_status mf_bank_quantize_rows(mf_plan_t plan, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
+                                int on_device);
+
+/* Storage type of the weighted data w s~ that the filter reads (Eq. 2):
+ * MF_F32 (default) or the bank's own 16-bit type.  With 16-bit data each
+ * mf_filter quantises w s~ per detector with a power-of-two scale c_d
+ * (max |c_d w s~| in [2^14, 2^15)) and the epilogue removes c_d exactly;
+ * products and transforms stay float32.  A 16-bit type other than the bank's
+ * makes mf_filter fail with MF_EINVAL.  Plans built with another filter
+ * implementation switch to the TMA-staged one.  Errors: MF_EINVAL, MF_ENOMEM. */
+mf_status mf_set_data_dtype(mf_plan_t plan, mf_dtype dtype);
+
+/* Per-row analysed ranges for plans whose rows are overlapping segments of
+ * longer data (Sec. V.C: the data are analysed in overlapping segments): row
+ * d keeps only samples in [range[2d], range[2d+1]) (host int64 [2 n_det],
+ * 0 <= begin <= end <= N; copied), replacing the plan's valid range for
+ * every row; NULL restores it.  Plans built with another filter
+ * implementation switch to the TMA-staged one.  Errors: MF_EINVAL, MF_ENOMEM. */
+mf_status mf_set_row_valid(mf_plan_t plan, const int64_t* range);
+
+/* Templates per pass-1/pass-2 launch pair (the batch; default: as many as
+ * fit a 256 MB intermediate).  Reallocates the intermediate (batch x n_det x
+ * N x 8 bytes).  Errors: MF_EINVAL (batch < 1), MF_ENOMEM. */
+mf_status mf_set_batch(mf_plan_t plan, int32_t batch);
 
 /* sigma_t^2 of templates 0..n-1 (float64, Eq. 2) into host out[n]; synchronises. */
 mf_status mf_get_sigmasq(mf_plan_t plan, double* out, int64_t n);
@@ -259,6 +293,87 @@ mf_status mf_mlp_topk(mf_mlp_t net, const float* x, const int32_t* n_valid, int6
                       int32_t* out, int32_t* count);
 /* Message of the last failed call on this network. */
 const char* mf_mlp_last_error(mf_mlp_t net);
+
+/* ---- long data in overlapping segments, by template-length class ------- */
+
+/* The data of every detector are a long stream (n_samples samples) analysed
+ * in overlapping segments (Sec. V.C).  Templates are grouped by duration into
+ * length classes; class c holds templates of at most class_len[c] seconds and
+ * filters them in segments of N_c samples (a power of two in [2^12, 2^20],
+ * picked by mf_batch_autotune or set with mf_batch_set_segment).  With
+ * L_c = class_len[c] fs rounded up to whole windows and stride
+ * S_c = N_c - L_c rounded down to whole windows, segment s starts at sample
+ * s S_c and analyses its local samples [L_c, min(L_c + S_c, n_samples - s S_c)):
+ * the first L_c samples are where the circular filter wraps the template
+ * around, and windows never straddle two segments.  Data past the end of the
+ * stream are zero.  Every class is one plan (mf_batch_plan) whose data rows
+ * are (segment, detector) pairs, row = s n_det + d; the batch owns it, sets
+ * its PSD and row ranges, and the caller loads its bank at N_c (mf_bank_*).
+ * Triggers are one per (detector, class, template, window of the stream). */
+typedef struct mf_batch_s* mf_batch_t;
+
+typedef struct {
+  double fs;                /* sampling rate of the stream, Hz */
+  int32_t n_det;            /* detectors, 1..8 */
+  int64_t n_samples;        /* samples per detector */
+  double f_low, f_high;     /* analysis band, Hz */
+  double snr_thr;           /* rho threshold (Sec. II, inclusive) */
+  int64_t window;           /* clustering window, samples */
+  int32_t n_class;          /* length classes, 1..8 */
+  const double* class_len;  /* host [n_class]: template duration bound of each class, s, increasing; copied */
+  int64_t max_triggers;     /* trigger capacity of each class */
+  void* cuda_stream;        /* stream that orders mf_batch_run with the caller's work */
+} mf_batch_desc;
+
+typedef struct {
+  int32_t det, cls, tmpl;   /* detector, length class, template id within the class's bank */
+  int32_t reserved;
+  int64_t sample;           /* window peak, sample index in the stream */
+  float snr, phase;         /* rho and arg z (quantised to 2 pi / 2048) */
+} mf_batch_trigger;
+
+enum { MF_RUN_SERIAL = 0, MF_RUN_STREAMS = 1, MF_RUN_GRAPH = 2 };
+
+mf_status mf_batch_create(mf_batch_t* out, const mf_batch_desc* desc);
+void mf_batch_destroy(mf_batch_t batch);
+const char* mf_batch_last_error(mf_batch_t batch);
+
+/* One-sided PSD on the grid of n_psd samples (host float64 [n_psd/2+1];
+ * n_psd a power of two >= every N_c; copied): class c uses bins k n_psd/N_c. */
+mf_status mf_batch_set_psd(mf_batch_t batch, const double* psd, int64_t n_psd);
+
+/* Segment length of class c (power of two, > L_c + window, <= 2^20), with
+ * templates per launch (0: the plan's default).  Creates the class's plan;
+ * a plan of another length is destroyed with its bank. */
+mf_status mf_batch_set_segment(mf_batch_t batch, int32_t cls, int64_t n, int32_t templates_per_launch);
+
+/* Autotuner: for every class whose template count n_tmpl[c] > 0, time the
+ * filter kernels on the actual row count of each admissible segment length
+ * (probe banks of zeros, no triggers) and launch batch, and keep the pair
+ * with the least estimated time per run, n_tmpl[c] x rows(N) x time per
+ * series; then as mf_batch_set_segment.  Needs the PSD.  Synchronises. */
+mf_status mf_batch_autotune(mf_batch_t batch, const int64_t* n_tmpl);
+
+/* Geometry of class c: N_c, L_c, S_c, segments, and the estimated and
+ * measured milliseconds per run (measured: of the last MF_RUN_SERIAL run; 0 if none). */
+mf_status mf_batch_segment(mf_batch_t batch, int32_t cls, int64_t* n, int64_t* tmpl_len, int64_t* stride,
+                           int64_t* n_seg, double* est_ms, double* run_ms);
+
+/* The class's plan (owned by the batch; valid until its segment length changes). */
+mf_status mf_batch_plan(mf_batch_t batch, int32_t cls, mf_plan_t* plan);
+
+/* Filter the stream with every class that has a bank: strain device float32
+ * [n_det][ld], n_samples used per row.  MF_RUN_SERIAL: classes one after the
+ * other; MF_RUN_STREAMS: each class on its own stream, joined at the end;
+ * MF_RUN_GRAPH: as STREAMS, captured once into a CUDA graph per (strain, ld)
+ * and replayed (the first run of a batch, or after a bank change, runs
+ * uncaptured first).  Asynchronous on the batch's stream. */
+mf_status mf_batch_run(mf_batch_t batch, const float* strain, int64_t ld, int32_t mode);
+
+/* Triggers of the last run into host out[cap], ordered by (class, detector,
+ * template, sample); *n_found = total.  Synchronises.  MF_EOVERFLOW as for
+ * mf_get_triggers. */
+mf_status mf_batch_get_triggers(mf_batch_t batch, mf_batch_trigger* out, int64_t cap, int64_t* n_found);
 
 /* ---- filtering without device allocation ------------------------------- */
 

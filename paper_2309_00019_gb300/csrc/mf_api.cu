@@ -41,6 +41,11 @@ struct mf_plan_s {
   // filter work space
   float2* q = nullptr;
   int64_t ld_q = 0;
+  mf_dtype data_dtype = MF_F32;   // storage of the weighted data the filter reads
+  void* q_lp = nullptr;           // 16-bit weighted data [n_det][ld_q]
+  unsigned* dmax = nullptr;       // per-detector max |q| (float bits)
+  float* dscale = nullptr;        // per-detector power-of-two data scale
+  int2* row_valid = nullptr;      // per-row analysed range (overlapping segments), or null
   float2* scratch = nullptr;
   int batch = 1;
   unsigned long long* slots = nullptr;
@@ -88,6 +93,35 @@ struct mf_plan_s {
   };
   std::vector<Sample> samples;      // batch samples awaiting read
 };
+
+namespace mf {
+int64_t plan_templates(const mf_plan_s* p) { return p ? p->n_tmpl : 0; }
+
+uint64_t plan_fingerprint(const mf_plan_s* p) {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the values a captured filter depends on
+  auto mix = [&](uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)(uintptr_t)p->bank);
+  mix((uint64_t)p->n_tmpl);
+  mix((uint64_t)p->batch);
+  mix((uint64_t)p->data_dtype);
+  mix((uint64_t)(uintptr_t)p->row_valid);
+  mix((uint64_t)(uintptr_t)p->scratch);
+  mix((uint64_t)(uintptr_t)p->slots);
+  mix((uint64_t)p->impl);
+  return h;
+}
+
+bool plan_capturable(const mf_plan_s* p) {
+  if (!p || !p->scale_valid || (p->impl != 1 && !p->maps_valid) || p->prof) return false;
+  const int64_t need = (int64_t)p->d.n_det * p->n_tmpl * p->n_win;
+  return p->slots_cap >= need && p->sel_cap >= p->n_tmpl && p->bc_cap >= mf::compact_blocks(need);
+}
+}  // namespace mf
 
 namespace {
 constexpr int kProfBatches = 1024;
@@ -232,7 +266,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   if (!is_pow2(d.n) || d.n < (1 << 12) || d.n > mf::kMaxN)
     return fail(nullptr, MF_EINVAL, "mf_plan: n must be a power of two in [2^12, 2^20]");
   if (!(d.fs > 0) || !std::isfinite(d.fs)) return fail(nullptr, MF_EINVAL, "mf_plan: fs must be positive");
-  if (d.n_det < 1 || d.n_det > 8) return fail(nullptr, MF_EINVAL, "mf_plan: n_det must be in 1..8");
+  if (d.n_det < 1 || d.n_det > 65536) return fail(nullptr, MF_EINVAL, "mf_plan: n_det must be in 1..65536");
   if (!(d.f_low >= 0) || !(d.f_high > d.f_low)) return fail(nullptr, MF_EINVAL, "mf_plan: need 0 <= f_low < f_high");
   if (d.dtype != MF_F32 && d.dtype != MF_F16 && d.dtype != MF_BF16) return fail(nullptr, MF_EINVAL, "mf_plan: dtype");
   if (!(d.snr_thr > 0) || !std::isfinite(d.snr_thr)) return fail(nullptr, MF_EINVAL, "mf_plan: snr_thr must be > 0");
@@ -263,7 +297,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   if (const char* v = std::getenv("MF_FUSED_SLOTS")) p->fz_slots = std::max(2, std::atoi(v));
   p->fz_B = (int)std::max<int64_t>(1, std::min<int64_t>(budget / (per * p->fz_slots), 4096));
   if (const char* v = std::getenv("MF_FUSED_B")) p->fz_B = std::max(1, std::atoi(v));
-  const int64_t scratch_series = std::max<int64_t>(p->batch, (int64_t)p->fz_B * p->fz_slots);
+  const int64_t scratch_series = p->impl == 3 ? std::max<int64_t>(p->batch, (int64_t)p->fz_B * p->fz_slots) : p->batch;
   mf_status s;
   if ((s = dalloc(p, &p->w_dev, p->nb * sizeof(double), "weights")) != MF_OK ||
       (s = dalloc(p, &p->q, (size_t)d.n_det * p->ld_q * sizeof(float2), "weighted data")) != MF_OK ||
@@ -295,6 +329,7 @@ void mf_destroy(mf_plan_t p) {
   dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev); dfree(p->ratio_dev); dfree(p->thr_raw_dev);
   dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
+  dfree(p->q_lp); dfree(p->dmax); dfree(p->dscale); dfree(p->row_valid);
   dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4); dfree(p->fz_counters);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -374,6 +409,91 @@ mf_status mf_bank_set_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const void
   return MF_OK;
 }
 
+mf_status mf_bank_quantize_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
+                                int on_device) {
+  if (!p || !htilde) return fail(p, MF_EINVAL, "mf_bank_quantize_rows: null argument");
+  if (!p->bank) return fail(p, MF_ESTATE, "mf_bank_quantize_rows: no bank reserved");
+  if (p->bank_dtype == MF_F32) return fail(p, MF_ESTATE, "mf_bank_quantize_rows: the bank is MF_F32");
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > p->n_tmpl)
+    return fail(p, MF_EINVAL, "mf_bank_quantize_rows: rows out of range");
+  if (ld < p->nb) return fail(p, MF_EINVAL, "mf_bank_quantize_rows: ld must be >= N/2+1");
+  if (n_rows == 0) return MF_OK;
+  const float2* src = (const float2*)htilde;
+  float2* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {  // stage host rows through a temporary device buffer
+    mf_status s = dalloc(p, &tmp, (size_t)n_rows * ld * sizeof(float2), "quantisation staging");
+    if (s != MF_OK) return s;
+    e = cudaMemcpyAsync(tmp, htilde, (size_t)n_rows * ld * sizeof(float2), cudaMemcpyHostToDevice, p->st);
+    src = tmp;
+  }
+  const size_t eb = elem_bytes(p->bank_dtype);
+  if (e == cudaSuccess)
+    e = mf::launch_quant_bank(src, ld, n_rows, p->nb, bank_type(p->bank_dtype), (char*)p->bank + (size_t)row0 * p->ld_bank * eb,
+                              p->ld_bank, p->scales_dev + row0, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  dfree(tmp);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_quantize_rows");
+  mf_status s = recompute_sigmasq(p, row0, n_rows);
+  if (s != MF_OK) return s;
+  e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_quantize_rows sigma^2");
+  return MF_OK;
+}
+
+mf_status mf_set_data_dtype(mf_plan_t p, mf_dtype dtype) {
+  if (!p) return fail(p, MF_EINVAL, "mf_set_data_dtype: null plan");
+  if (dtype != MF_F32 && dtype != MF_F16 && dtype != MF_BF16) return fail(p, MF_EINVAL, "mf_set_data_dtype: dtype");
+  cudaStreamSynchronize(p->st);
+  if (dtype != MF_F32) {
+    mf_status s;
+    if (!p->q_lp && (s = dalloc(p, &p->q_lp, (size_t)p->d.n_det * p->ld_q * 4, "16-bit weighted data")) != MF_OK) return s;
+    if (!p->dmax && (s = dalloc(p, &p->dmax, (size_t)p->d.n_det * sizeof(unsigned), "data maxima")) != MF_OK) return s;
+    if (!p->dscale && (s = dalloc(p, &p->dscale, (size_t)p->d.n_det * sizeof(float), "data scales")) != MF_OK) return s;
+    cudaError_t e = cudaMemsetAsync(p->q_lp, 0, (size_t)p->d.n_det * p->ld_q * 4, p->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_data_dtype");
+    p->impl = 2;
+  }
+  p->data_dtype = dtype;
+  p->maps_valid = false;
+  return MF_OK;
+}
+
+mf_status mf_set_row_valid(mf_plan_t p, const int64_t* range) {
+  if (!p) return fail(p, MF_EINVAL, "mf_set_row_valid: null plan");
+  cudaStreamSynchronize(p->st);
+  if (!range) {
+    dfree(p->row_valid);
+    return MF_OK;
+  }
+  std::vector<int2> r(p->d.n_det);
+  for (int i = 0; i < p->d.n_det; ++i) {
+    const int64_t b = range[2 * i], e = range[2 * i + 1];
+    if (b < 0 || e < b || e > p->d.n) return fail(p, MF_EINVAL, "mf_set_row_valid: need 0 <= begin <= end <= N");
+    r[i] = make_int2((int)b, (int)e);
+  }
+  mf_status s;
+  if (!p->row_valid && (s = dalloc(p, &p->row_valid, r.size() * sizeof(int2), "row ranges")) != MF_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(p->row_valid, r.data(), r.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_row_valid");
+  p->impl = 2;
+  return MF_OK;
+}
+
+mf_status mf_set_batch(mf_plan_t p, int32_t batch) {
+  if (!p) return fail(p, MF_EINVAL, "mf_set_batch: null plan");
+  if (batch < 1) return fail(p, MF_EINVAL, "mf_set_batch: batch must be >= 1");
+  cudaStreamSynchronize(p->st);
+  const int64_t per = (int64_t)p->d.n_det * p->d.n * (int64_t)sizeof(float2);
+  const int64_t series = p->impl == 3 ? std::max<int64_t>(batch, (int64_t)p->fz_B * p->fz_slots) : batch;
+  mf_status s = dalloc(p, &p->scratch, (size_t)series * per, "scratch");
+  if (s != MF_OK) return s;
+  p->batch = batch;
+  return MF_OK;
+}
+
 mf_status mf_load_bank(mf_plan_t p, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld, const float* scales,
                        int on_device) {
   if (!p || !htilde) return fail(p, MF_EINVAL, "mf_load_bank: null argument");
@@ -418,6 +538,8 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   if (ld_dtilde < p->nb) return fail(p, MF_EINVAL, "mf_filter: ld_dtilde < N/2+1");
   if (n_subset < 0 && subset) return fail(p, MF_EINVAL, "mf_filter: n_subset < 0 (all templates) needs subset NULL");
   if (n_subset > 0 && !subset) return fail(p, MF_EINVAL, "mf_filter: subset is NULL");
+  if (p->data_dtype != MF_F32 && p->data_dtype != p->bank_dtype)
+    return fail(p, MF_EINVAL, "mf_filter: 16-bit data need a bank of the same 16-bit type");
   const int64_t n_sel = n_subset < 0 ? p->n_tmpl : n_subset;
   mf_status s = ensure_slots(p, std::max<int64_t>(n_sel, 1));
   if (s != MF_OK) return s;
@@ -432,6 +554,10 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   e = mf::launch_prep((const float2*)dtilde, ld_dtilde, p->w_dev, p->nb, p->d.n_det, p->q, p->ld_q, p->slots, n_slots,
                       p->st, 1.0 / p->sigma_ref);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter prep");
+  if (p->data_dtype != MF_F32) {
+    e = mf::launch_quant_q(p->q, p->ld_q, p->nb, p->d.n_det, bank_type(p->data_dtype), p->q_lp, p->dmax, p->dscale, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter data quantisation");
+  }
   mf::FilterArgs a{};
   a.n = p->d.n;
   a.n1 = p->n1;
@@ -460,6 +586,10 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.tw1 = p->tw;
   a.tw2 = p->tw + 1024;
   a.tw4 = p->tw4;
+  a.row_valid = p->row_valid;
+  a.q_type = bank_type(p->data_dtype);
+  a.q_lp = p->q_lp;
+  a.dscale = p->dscale;
   if (p->impl != 1 && !p->maps_valid) {
     e = mf::filter2_encode_maps(a, p->n_tmpl, &p->maps);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter tensor maps");

@@ -93,24 +93,39 @@ struct RawEpi {
   const int32_t* sel;
   const float* ratio;
   const float* thr_raw;
+  const float* dscale;  // per detector: power-of-two scale of 16-bit data (z' carries it), or null
   int64_t pos0;
   int n_det;
   int64_t window, vb, ve, n_win, n_sel_total;
   unsigned long long* slots;
+  const int2* row_valid;  // per data row [begin, end), or null: [vb, ve) for every row
   struct Ser {
     float ratio, thr;
+    int vb, ve;
     unsigned long long* slot;
   };
   __device__ __forceinline__ Ser series(int s) const {
     const int d = s % n_det;
     const int64_t pos = pos0 + s / n_det;
     const int t = sel[pos];
-    return Ser{__ldg(ratio + t), __ldg(thr_raw + t), slots + ((int64_t)d * n_sel_total + pos) * n_win};
+    float r = __ldg(ratio + t), th = __ldg(thr_raw + t);
+    if (dscale) {  // exact: c is a power of two
+      const float c = __ldg(dscale + d);
+      r /= c;
+      th *= c * c;
+    }
+    int b = (int)vb, e = (int)ve;
+    if (row_valid) {
+      const int2 rv = __ldg(row_valid + d);
+      b = rv.x;
+      e = rv.y;
+    }
+    return Ser{r, th, b, e, slots + ((int64_t)d * n_sel_total + pos) * n_win};
   }
   __device__ __forceinline__ void operator()(const Ser& se, int64_t n, float2 z) const {
     const float m2 = fmaf(z.x, z.x, z.y * z.y);
     if (m2 >= se.thr) {
-      if (n >= vb && n < ve) {
+      if (n >= se.vb && n < se.ve) {
         const float a = z.x * se.ratio, b = z.y * se.ratio;
         record_peak(se.slot, n, window, a, b, fmaf(a, a, b * b));
       }

@@ -53,7 +53,7 @@ struct Xch {
 // item's TMA tiles (template + weighted data) and then, once those are in
 // registers, the padded exchange buffer of the same item; the next item's
 // tiles land in the other slot.  Then the sub-FFT twiddle table and barriers.
-template <int N1, int BT>
+template <int N1, int BT, int QT = kBankF32>
 struct ColGeo {
   using G = SubFft<N1>;
   static constexpr int C = kT2 / G::T;                    // columns per item
@@ -61,8 +61,9 @@ struct ColGeo {
   static constexpr int BOXR = ROWS < 256 ? ROWS : 256;    // rows per TMA box
   static constexpr int NBOX = ROWS / BOXR;
   static constexpr int HB = BT == kBankF32 ? 8 : 4;       // bytes per template element
+  static constexpr int QB = QT == kBankF32 ? 8 : 4;       // bytes per weighted-data element
   static constexpr int H_BYTES = ROWS * C * HB;
-  static constexpr int Q_BYTES = ROWS * C * 8;
+  static constexpr int Q_BYTES = ROWS * C * QB;
   static constexpr int K = C >= 16 ? 1 : 16 / C;
   using X = Xch<N1, K, false>;
   static constexpr int XCH_BYTES = C * X::S * 8;
@@ -123,11 +124,11 @@ __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity, int* st
 // pass 1
 // ---------------------------------------------------------------------------
 
-template <int N1, int N2, int BT>
+template <int N1, int N2, int BT, int QT>
 __global__ void __launch_bounds__(kT2, 3)
     k_cols(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUtensorMap tm_q, FilterArgs a) {
   using G = SubFft<N1>;
-  using P = ColGeo<N1, BT>;
+  using P = ColGeo<N1, BT, QT>;
   using X = typename P::X;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C;
   constexpr int NCB = N2 / C;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kT2, 3)
 #pragma unroll
     for (int bx = 0; bx < P::NBOX; ++bx) {
       tma_load_3d_hint(dst + bx * P::BOXR * C * P::HB, &tm_h, cb * C, bx * P::BOXR, tmpl, bar + slot, pol_stream);
-      tma_load_3d(dst + P::H_BYTES + bx * P::BOXR * C * 8, &tm_q, cb * C, bx * P::BOXR, d, bar + slot);
+      tma_load_3d(dst + P::H_BYTES + bx * P::BOXR * C * P::QB, &tm_q, cb * C, bx * P::BOXR, d, bar + slot);
     }
   };
   pdl_launch_dependents();  // the next kernel may start its prologue as our CTAs retire
@@ -176,7 +177,6 @@ __global__ void __launch_bounds__(kT2, 3)
     // every thread waits (bounded) for this item's tiles, reads its inputs, then one barrier
     const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
     const unsigned char* sh = sm + slot * P::SLOT;
-    const float2* sq = reinterpret_cast<const float2*>(sh + P::H_BYTES);
     const int s = item / NCB;
     const int k2 = (item % NCB) * C + c;
     float2 v[RA];
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kT2, 3)
         v[r] = make_float2(0.f, 0.f);
       } else {
         const int idx = (t + r * RB) * C + c;
-        v[r] = cmulc(sq[idx], smem_h<BT>(sh, idx));
+        v[r] = cmulc(smem_h<QT>(sh + P::H_BYTES, idx), smem_h<BT>(sh, idx));
       }
     }
     // tiles consumed by every thread; the previous item (other slot) is finished too
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
     if ((int)blockIdx.x < n_items) issue(blockIdx.x, 0);
   }
   if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) return;
-  RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, a.pos0, a.n_det, a.window, a.valid_begin, a.valid_end,
-            a.n_win, a.n_sel_total, a.slots};
+  RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, a.q_type == kBankF32 ? nullptr : a.dscale, a.pos0, a.n_det, a.window, a.valid_begin, a.valid_end,
+            a.n_win, a.n_sel_total, a.slots, a.row_valid};
   int k = 0;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
@@ -732,10 +732,10 @@ int grid2(int items) {
   return items < g ? items : g;
 }
 
-template <int N1, int N2, int BT>
+template <int N1, int N2, int BT, int QT>
 cudaError_t run_cols(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st) {
-  using P = ColGeo<N1, BT>;
-  auto k = k_cols<N1, N2, BT>;
+  using P = ColGeo<N1, BT, QT>;
+  auto k = k_cols<N1, N2, BT, QT>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem2(k, P::SMEM);
@@ -748,12 +748,20 @@ cudaError_t run_cols(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st)
   return e;
 }
 
+// (bank, data) storage pairs: FP32 data with any bank; 16-bit data with a bank of the same type
 template <int N1, int N2>
 cudaError_t run_cols_bt(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st) {
-  switch (a.bank_type) {
-    case kBankF32: return run_cols<N1, N2, kBankF32>(a, m, st);
-    case kBankF16: return run_cols<N1, N2, kBankF16>(a, m, st);
-    case kBankBF16: return run_cols<N1, N2, kBankBF16>(a, m, st);
+  if (a.q_type == kBankF32) {
+    switch (a.bank_type) {
+      case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32>(a, m, st);
+      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32>(a, m, st);
+      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32>(a, m, st);
+    }
+  } else if (a.q_type == a.bank_type) {
+    switch (a.bank_type) {
+      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF16>(a, m, st);
+      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankBF16>(a, m, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -906,7 +914,9 @@ cudaError_t filter2_encode_maps(const FilterArgs& a, int64_t n_tmpl, Filter2Maps
   if (!encode_view(&m->h, a.bank, f32 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, f32 ? 8 : 4,
                    n2, rows, n_tmpl, a.ld_bank, C, boxr))
     return cudaErrorInvalidValue;
-  if (!encode_view(&m->q, a.q, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, n2, rows, a.n_det, a.ld_q, C, boxr))
+  const bool q32 = a.q_type == kBankF32;
+  if (!encode_view(&m->q, q32 ? (const void*)a.q : a.q_lp, q32 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                   q32 ? 8 : 4, n2, rows, a.n_det, a.ld_q, C, boxr))
     return cudaErrorInvalidValue;
   m->ok = true;
   return cudaSuccess;

@@ -8,6 +8,8 @@
 
 #include <string>
 
+struct mf_plan_s;  // the plan (defined by the C-ABI layer)
+
 namespace mf {
 
 // Packed per-window maximum: [63:32] float bits of rho^2 (>= 0, so integer
@@ -51,6 +53,13 @@ struct FilterArgs {
   const float* thr_raw;     // per template: rho_thr^2 / ratio^2 on the pre-scaled data (TMA kernels)
   const float2* tw4;        // four-step twiddles w_N^m, m < RA(N1) * N2 (TMA kernels)
   int first_batch;          // 1: the weighted data were written by the kernel just before (PDL ordering)
+  // 16-bit weighted data (TMA kernels): q_lp [n_det][ld_q] half2 / bfloat162 holding c_d q, with
+  // c_d = dscale[d] a power of two; q_type = kBankF32 means the FP32 q above is used
+  int q_type;
+  const void* q_lp;
+  const float* dscale;
+  // per data row analysed range [x, y) (TMA kernels), or null: [valid_begin, valid_end) for all rows
+  const int2* row_valid;
 };
 
 // Tensor maps of the TMA-staged filter: template bank and weighted data, each
@@ -60,6 +69,24 @@ struct Filter2Maps {
   CUtensorMap q;
   bool ok = false;
 };
+// Quantise the FP32 weighted data q [n_det][ld_q] (nb bins per detector) to
+// 16-bit (q_type) q_lp with a per-detector power-of-two scale c_d chosen so that
+// max |c_d q| is in [2^14, 2^15); writes dscale[d] = c_d.  dmax: n_det words of
+// scratch.
+cudaError_t launch_quant_q(const float2* q, int64_t ld_q, int64_t nb, int n_det, int q_type, void* q_lp,
+                           unsigned* dmax, float* dscale, cudaStream_t st);
+// Quantise n_rows FP32 templates (src [n_rows][ld_src], nb bins) to the 16-bit
+// bank rows dst [n_rows][ld_dst] with a per-template power-of-two scale:
+// stored = h / scale, max |stored| in [2^14, 2^15); scales[i] = scale.
+cudaError_t launch_quant_bank(const float2* src, int64_t ld_src, int64_t n_rows, int64_t nb, int bank_type, void* dst,
+                              int64_t ld_dst, float* scales, cudaStream_t st);
+// Plan introspection for the length-class runner (mf_batch.cu): templates in
+// the bank; a fingerprint of everything a captured graph of mf_filter bakes in
+// (buffers, batch, storage types); and whether mf_filter on the whole bank would
+// run without host synchronisation or allocation (so that it can be captured).
+int64_t plan_templates(const ::mf_plan_s* p);
+uint64_t plan_fingerprint(const ::mf_plan_s* p);
+bool plan_capturable(const ::mf_plan_s* p);
 cudaError_t filter2_encode_maps(const FilterArgs& a, int64_t n_tmpl, Filter2Maps* m);
 cudaError_t launch_filter2_pass1(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);

@@ -12,6 +12,8 @@
 // frequency half), multiplies by exp(+2 pi i j1 k2 / N) and writes an
 // L2-resident scratch; pass 2 does N2-point row transforms and evaluates
 // rho^2 of z[j1 + N1 j2] in registers, so the SNR series never reaches memory.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -484,6 +486,84 @@ __global__ void k_compact_write(const unsigned long long* __restrict__ slots, in
   }
 }
 
+
+// --- 16-bit storage (bank and weighted data) ---------------------------------
+
+// Power-of-two c with amax * c in [2^14, 2^15) (1 for amax = 0 or not finite):
+// the largest 16-bit value then stays below FP16's 65504 with room for rounding,
+// and scaling by c is exact in binary floating point.
+__device__ __forceinline__ float pow2_scale(float amax) {
+  if (!(amax > 0.f) || !(amax < INFINITY)) return 1.f;
+  const int E = (int)((__float_as_uint(amax) >> 23) & 0xffu);  // amax < 2^(E - 126)
+  int e = 141 - E;                                              // amax c < 2^15, >= 2^14 (normal amax)
+  e = e > 126 ? 126 : (e < -126 ? -126 : e);
+  return __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
+template <int QT>
+__device__ __forceinline__ void store_lp(void* base, int64_t i, float x, float y) {
+  if constexpr (QT == kBankF16) {
+    reinterpret_cast<__half2*>(base)[i] = __floats2half2_rn(x, y);
+  } else {
+    reinterpret_cast<__nv_bfloat162*>(base)[i] = __floats2bfloat162_rn(x, y);
+  }
+}
+
+__device__ __forceinline__ float block_max(float m, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
+// grid (blocks, n_det): per-detector max |component| of q into dmax (float bits, >= 0)
+__global__ void k_qmax(const float2* __restrict__ q, int64_t ld_q, int64_t nb, unsigned* dmax) {
+  __shared__ float red[32];
+  const int d = blockIdx.y;
+  float m = 0.f;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = q[(int64_t)d * ld_q + k];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(dmax + d, __float_as_uint(m));
+}
+
+template <int QT>
+__global__ void k_quant_q(const float2* __restrict__ q, int64_t ld_q, int64_t nb, const unsigned* __restrict__ dmax,
+                          void* q_lp, float* dscale) {
+  const int d = blockIdx.y;
+  const float c = pow2_scale(__uint_as_float(dmax[d]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) dscale[d] = c;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = q[(int64_t)d * ld_q + k];
+    store_lp<QT>(q_lp, (int64_t)d * ld_q + k, v.x * c, v.y * c);
+  }
+}
+
+// one CTA per template row
+template <int BT>
+__global__ void k_quant_bank(const float2* __restrict__ src, int64_t ld_src, int64_t nb, void* dst, int64_t ld_dst,
+                             float* scales) {
+  __shared__ float red[32];
+  const float2* row = src + blockIdx.x * ld_src;
+  float m = 0.f;
+  for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
+    const float2 v = row[k];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  const float c = pow2_scale(block_max(m, red));
+  for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
+    const float2 v = row[k];
+    store_lp<BT>(dst, blockIdx.x * ld_dst + k, v.x * c, v.y * c);
+  }
+  if (threadIdx.x == 0) scales[blockIdx.x] = 1.f / c;  // exact: c is a power of two
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -529,6 +609,34 @@ cudaError_t launch_rfft(const float* x, int64_t ld_s, int n_det, int64_t n, int 
   (void)n1;
   (void)n2;
   MF_DISPATCH_N(n, run_rfft, (x, ld_s, n_det, dt, scratch, out, ld_d, st))
+}
+
+cudaError_t launch_quant_q(const float2* q, int64_t ld_q, int64_t nb, int n_det, int q_type, void* q_lp,
+                           unsigned* dmax, float* dscale, cudaStream_t st) {
+  if (q_type != kBankF16 && q_type != kBankBF16) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(dmax, 0, n_det * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const dim3 g((unsigned)std::max(1, std::min<int>(num_sms() * 2 / n_det + 1, (int)((nb + 255) / 256))), (unsigned)n_det);
+  k_qmax<<<g, 256, 0, st>>>(q, ld_q, nb, dmax);
+  if (q_type == kBankF16)
+    k_quant_q<kBankF16><<<g, 256, 0, st>>>(q, ld_q, nb, dmax, q_lp, dscale);
+  else
+    k_quant_q<kBankBF16><<<g, 256, 0, st>>>(q, ld_q, nb, dmax, q_lp, dscale);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_bank(const float2* src, int64_t ld_src, int64_t n_rows, int64_t nb, int bank_type, void* dst,
+                              int64_t ld_dst, float* scales, cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  if (bank_type == kBankF16)
+    k_quant_bank<kBankF16><<<(unsigned)n_rows, 256, 0, st>>>(src, ld_src, nb, dst, ld_dst, scales);
+  else if (bank_type == kBankBF16)
+    k_quant_bank<kBankBF16><<<(unsigned)n_rows, 256, 0, st>>>(src, ld_src, nb, dst, ld_dst, scales);
+  else
+    return cudaErrorInvalidValue;
+  ++g_launches;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sigmasq(const void* bank, int bank_type, int64_t ld_bank, const float* scales, int64_t row0,

@@ -51,6 +51,21 @@ class mf_plan_stats(C.Structure):
                 ("fused_ms", C.c_double), ("impl", C.c_int32), ("batch", C.c_int32)]
 
 
+class mf_batch_desc(C.Structure):
+    _fields_ = [("fs", C.c_double), ("n_det", C.c_int32), ("n_samples", C.c_int64), ("f_low", C.c_double),
+                ("f_high", C.c_double), ("snr_thr", C.c_double), ("window", C.c_int64), ("n_class", C.c_int32),
+                ("class_len", C.POINTER(C.c_double)), ("max_triggers", C.c_int64), ("cuda_stream", C.c_void_p)]
+
+
+class mf_batch_trigger(C.Structure):
+    _fields_ = [("det", C.c_int32), ("cls", C.c_int32), ("tmpl", C.c_int32), ("reserved", C.c_int32),
+                ("sample", C.c_int64), ("snr", C.c_float), ("phase", C.c_float)]
+
+
+MF_RUN_SERIAL, MF_RUN_STREAMS, MF_RUN_GRAPH = 0, 1, 2
+BATCH_TRIGGER_NP = np.dtype([("det", np.int32), ("cls", np.int32), ("tmpl", np.int32), ("reserved", np.int32),
+                             ("sample", np.int64), ("snr", np.float32), ("phase", np.float32)])
+
 TRIGGER_NP = np.dtype([("det", np.int32), ("tmpl", np.int32), ("sample", np.int64), ("snr", np.float32),
                        ("phase", np.float32)])
 COINC_NP = np.dtype([("tmpl", np.int32), ("shift", np.int32), ("sample0", np.int64), ("sample1", np.int64),
@@ -70,6 +85,21 @@ SIGNATURES = {
     "mf_bank_reserve": (C.c_int, [_P, C.c_int, _I64]),
     "mf_bank_set_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, _P, C.c_int]),
     "mf_get_sigmasq": (C.c_int, [_P, _P, _I64]),
+    "mf_bank_quantize_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, C.c_int]),
+    "mf_set_data_dtype": (C.c_int, [_P, C.c_int]),
+    "mf_set_row_valid": (C.c_int, [_P, _P]),
+    "mf_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(mf_batch_desc)]),
+    "mf_batch_destroy": (None, [_P]),
+    "mf_batch_last_error": (C.c_char_p, [_P]),
+    "mf_batch_set_psd": (C.c_int, [_P, _P, _I64]),
+    "mf_batch_set_segment": (C.c_int, [_P, C.c_int32, _I64, C.c_int32]),
+    "mf_batch_autotune": (C.c_int, [_P, _P]),
+    "mf_batch_segment": (C.c_int, [_P, C.c_int32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64),
+                                   C.POINTER(_I64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mf_batch_plan": (C.c_int, [_P, C.c_int32, C.POINTER(_P)]),
+    "mf_batch_run": (C.c_int, [_P, _P, _I64, C.c_int32]),
+    "mf_batch_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
+    "mf_set_batch": (C.c_int, [_P, C.c_int32]),
     "mf_strain_to_fd": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_decimate": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_filter": (C.c_int, [_P, _P, _I64, _P, _I64]),
@@ -156,10 +186,19 @@ class Plan:
         self.n, self.nb, self.n_det, self.n_tmpl = n, n // 2 + 1, n_det, 0
         self.lib = lib
 
+    @classmethod
+    def borrowed(cls, handle, desc):
+        """A view of a plan owned by someone else (a Batch): never destroyed here."""
+        self = cls.__new__(cls)
+        self.h, self.desc, self.lib = handle, desc, load()
+        self.n, self.nb, self.n_det, self.n_tmpl = desc.n, desc.n // 2 + 1, desc.n_det, 0
+        self._borrowed = True
+        return self
+
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not getattr(self, "_borrowed", False):
             self.lib.mf_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -190,6 +229,24 @@ class Plan:
             on_device = 0 if isinstance(rows, np.ndarray) else int(rows.is_cuda)
         sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
         _check(self.h, self.lib.mf_bank_set_rows(self.h, row0, rows.shape[0], _ptr(rows), ld, _ptr(sc), on_device))
+
+    def bank_quantize_rows(self, row0, rows, ld=None, on_device=None):
+        """Quantise complex64 template rows into the plan's 16-bit bank."""
+        ld = rows.shape[1] if ld is None else ld
+        if on_device is None:
+            on_device = 0 if isinstance(rows, np.ndarray) else int(rows.is_cuda)
+        _check(self.h, self.lib.mf_bank_quantize_rows(self.h, row0, rows.shape[0], _ptr(rows), ld, on_device))
+
+    def set_data_dtype(self, dtype):
+        _check(self.h, self.lib.mf_set_data_dtype(self.h, dtype))
+
+    def set_row_valid(self, ranges):
+        """Per-row analysed ranges, int64 [n_det, 2] (None restores the plan's range)."""
+        r = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+        _check(self.h, self.lib.mf_set_row_valid(self.h, _ptr(r)))
+
+    def set_batch(self, batch):
+        _check(self.h, self.lib.mf_set_batch(self.h, batch))
 
     def sigmasq(self, n=None):
         n = self.n_tmpl if n is None else n
@@ -321,3 +378,80 @@ class MLP:
     def topk(self, x, n_valid, k, out, p_mass=2.0, count=None):
         self._chk(self.lib.mf_mlp_topk(self.h, _ptr(x), _ptr(n_valid), x.shape[0], k, p_mass, _ptr(out),
                                        _ptr(count)))
+
+
+def _bcheck(batch, st, ok=(MF_OK,)):
+    if st not in ok:
+        msg = load().mf_batch_last_error(batch)
+        raise MFError(st, msg.decode() if msg else "")
+    return st
+
+
+class Batch:
+    """Owner of one ``mf_batch_t``: long data in overlapping segments, one plan
+    per template-length class (include/mf.h)."""
+
+    def __init__(self, fs, n_det, n_samples, f_low, f_high, snr_thr, window, class_len, max_triggers=1 << 22,
+                 stream=None):
+        lib = load()
+        self._len = (C.c_double * len(class_len))(*class_len)
+        d = mf_batch_desc(fs=fs, n_det=n_det, n_samples=n_samples, f_low=f_low, f_high=f_high, snr_thr=snr_thr,
+                          window=window, n_class=len(class_len), class_len=self._len, max_triggers=max_triggers,
+                          cuda_stream=stream)
+        h = _P()
+        _bcheck(None, lib.mf_batch_create(C.byref(h), C.byref(d)))
+        self.h, self.desc, self.lib = h, d, lib
+        self.n_class = len(class_len)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_psd(self, psd, n_psd):
+        psd = np.ascontiguousarray(psd, dtype=np.float64)
+        assert len(psd) == n_psd // 2 + 1
+        _bcheck(self.h, self.lib.mf_batch_set_psd(self.h, psd.ctypes.data, n_psd))
+
+    def set_segment(self, cls, n, per_launch=0):
+        _bcheck(self.h, self.lib.mf_batch_set_segment(self.h, cls, n, per_launch))
+
+    def autotune(self, n_tmpl):
+        a = np.ascontiguousarray(n_tmpl, dtype=np.int64)
+        _bcheck(self.h, self.lib.mf_batch_autotune(self.h, a.ctypes.data))
+
+    def segment(self, cls):
+        v = [_I64() for _ in range(4)]
+        e, r = C.c_double(), C.c_double()
+        _bcheck(self.h, self.lib.mf_batch_segment(self.h, cls, *[C.byref(x) for x in v], C.byref(e), C.byref(r)))
+        return dict(n=v[0].value, tmpl_len=v[1].value, stride=v[2].value, n_seg=v[3].value, est_ms=e.value,
+                    run_ms=r.value)
+
+    def plan(self, cls):
+        """The class's plan (a borrowed Plan: load its bank with bank_reserve / bank_set_rows / ...)."""
+        h = _P()
+        _bcheck(self.h, self.lib.mf_batch_plan(self.h, cls, C.byref(h)))
+        g = self.segment(cls)
+        d = mf_plan_desc(fs=self.desc.fs, n=g["n"], n_det=g["n_seg"] * self.desc.n_det, f_low=self.desc.f_low,
+                         f_high=self.desc.f_high, dtype=MF_F32, snr_thr=self.desc.snr_thr, window=self.desc.window,
+                         valid_begin=g["tmpl_len"], valid_end=g["n"], max_triggers=self.desc.max_triggers,
+                         cuda_stream=None)
+        return Plan.borrowed(h, d)
+
+    def run(self, strain, ld=None, mode=MF_RUN_GRAPH):
+        ld = strain.shape[-1] if ld is None else ld
+        _bcheck(self.h, self.lib.mf_batch_run(self.h, _ptr(strain), ld, mode))
+
+    def triggers(self):
+        n = _I64(0)
+        _bcheck(self.h, self.lib.mf_batch_get_triggers(self.h, None, 0, C.byref(n)), ok=(MF_OK, MF_EOVERFLOW))
+        out = np.zeros(n.value, dtype=BATCH_TRIGGER_NP)
+        st = self.lib.mf_batch_get_triggers(self.h, out.ctypes.data if n.value else None, n.value, C.byref(n))
+        _bcheck(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
+        return out, n.value, st

@@ -39,6 +39,8 @@ from .configs import (  # noqa: F401
     Config2,
     make_config2,
     make_banks,
+    Config3,
+    make_config3,
     Config4,
     make_config4,
 )

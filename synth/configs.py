@@ -228,3 +228,80 @@ def make_config4(seed=4, n_tmpl=50000, n_inj=200, f_low=30.0):
                dt_hl=rng.uniform(-0.010, 0.010, n_inj), phi=rng.uniform(0, 2 * math.pi, (n_inj, 2)))
     return Config4(n=n, fs=fs, f_low=f_low, thr=5.5, window=int(fs), psd=g.psd_bins(n, fs), m1=m1, m2=m2,
                    noise_fd=noise, inj=inj)
+
+
+@dataclass
+class Config3:
+    """Uneven-length workload: a TaylorF2 bank with durations of seconds to
+    ~100 s, grouped into length classes, over long two-detector data."""
+    fs: float
+    n_samples: int
+    f_low: float
+    thr: float
+    window: int
+    class_len: tuple
+    m1: np.ndarray                # per template, ordered by class
+    m2: np.ndarray
+    duration: np.ndarray          # 2PN duration from f_low, s
+    cls: np.ndarray               # length class of each template
+    noise_fd: np.ndarray          # complex128 [2, n_fd/2+1] on the grid of n_fd >= n_samples samples
+    n_fd: int
+    inj: dict
+
+    def class_ids(self, c):
+        return np.flatnonzero(self.cls == c)
+
+    def psd(self, n):
+        return g.psd_bins(n, self.fs)
+
+    def strain(self, device):
+        """float32 torch tensor [2, n_samples] on device: noise plus injections
+        (evaluated there with ``taylorf2_torch`` on the n_fd grid)."""
+        import torch
+
+        dev = torch.device(device)
+        nb = self.n_fd // 2 + 1
+        fd = torch.from_numpy(self.noise_fd).to(dev)
+        f = torch.arange(nb, dtype=torch.float64, device=dev) * (self.fs / self.n_fd)
+        psd = torch.from_numpy(g.psd_bins(self.n_fd, self.fs)).to(dev)
+        w = torch.zeros(nb, dtype=torch.float64, device=dev)
+        band = (f >= self.f_low) & (torch.arange(nb, device=dev) < self.n_fd // 2) & (psd > 0)
+        w[band] = 4.0 * (self.fs / self.n_fd) / psd[band]
+        im1, im2 = self.inj["m1"], self.inj["m2"]
+        for b0 in range(0, len(im1), 8):
+            b1 = min(len(im1), b0 + 8)
+            h = g.taylorf2_torch(self.n_fd, self.fs, im1[b0:b1], im2[b0:b1], self.f_low, dev).to(torch.complex128)
+            sig = torch.sqrt((w[None, :] * (h.real ** 2 + h.imag ** 2)).sum(dim=1))
+            amp = torch.from_numpy(self.inj["snr"][b0:b1]).to(dev) / sig
+            for d in range(2):
+                t0 = torch.from_numpy(self.inj["tc"][b0:b1] + (self.inj["dt_hl"][b0:b1] if d == 1 else 0.0)).to(dev)
+                ph = torch.from_numpy(self.inj["phi"][b0:b1, d]).to(dev)
+                sh = torch.exp(-2j * math.pi * f[None, :] * t0[:, None] + 1j * ph[:, None])
+                fd[d] += (amp[:, None] * h * sh).sum(dim=0)
+            del h
+        x = torch.fft.irfft(fd, n=self.n_fd, dim=-1) * self.fs
+        return x[:, :self.n_samples].to(torch.float32).contiguous()
+
+
+def make_config3(seed=3, n_tmpl=20000, T=4096.0, fs=2048.0, f_low=25.0, class_len=(4.0, 16.0, 64.0, 256.0),
+                 n_inj=64, margin=1.1):
+    """20,000 TaylorF2 templates (chirp mass 1.2-10, durations ~2.5-91 s from
+    25 Hz) in 4/16/64/256 s length classes (the smallest class holding
+    margin x the 2PN duration), two detectors x 4096 s at 2048 Hz of coloured
+    noise with n_inj injections at SNR U(8, 20)."""
+    rng = np.random.default_rng(seed)
+    m1, m2, _, _ = g.sample_bank_chirp_times(rng, n_tmpl, f_low)
+    dur = g.duration_2pn(m1, m2, f_low)
+    cls = np.searchsorted(np.asarray(class_len), margin * dur, side="left")
+    keep = cls < len(class_len)
+    order = np.lexsort((np.arange(n_tmpl)[keep], cls[keep]))
+    m1, m2, dur, cls = m1[keep][order], m2[keep][order], dur[keep][order], cls[keep][order]
+    n_samples = int(T * fs)
+    n_fd = 1 << int(math.ceil(math.log2(n_samples)))
+    noise = np.stack([g.coloured_noise_fd(rng, n_fd, fs) for _ in range(2)])
+    im1, im2, _, _ = g.sample_bank_chirp_times(rng, n_inj, f_low)
+    inj = dict(m1=im1, m2=im2, snr=rng.uniform(8.0, 20.0, n_inj),
+               tc=np.sort(rng.uniform(100.0 + 0.1 * T, 0.98 * T, n_inj)), dt_hl=rng.uniform(-0.010, 0.010, n_inj),
+               phi=rng.uniform(0, 2 * math.pi, (n_inj, 2)))
+    return Config3(fs=fs, n_samples=n_samples, f_low=f_low, thr=5.5, window=int(fs), class_len=tuple(class_len),
+                   m1=m1, m2=m2, duration=dur, cls=cls.astype(np.int32), noise_fd=noise, n_fd=n_fd, inj=inj)

@@ -45,6 +45,8 @@ def test_struct_layouts(mflib):
     assert C.sizeof(mflib.mf_coinc) == 40
     assert C.sizeof(mflib.mf_plan_desc) == 96
     assert C.sizeof(mflib.mf_coinc_desc) == 48
+    assert C.sizeof(mflib.mf_batch_desc) == 88
+    assert C.sizeof(mflib.mf_batch_trigger) == 32 == mflib.BATCH_TRIGGER_NP.itemsize
 
 
 @pytest.mark.parametrize("field,value", [("n", 3000), ("n", 1 << 11), ("n", 1 << 21), ("n_det", 0), ("fs", 0.0),
@@ -68,3 +70,22 @@ def test_null_arguments_are_rejected_without_a_device(mflib):
     assert lib.mf_set_psd(None, None, 0) == mflib.MF_EINVAL
     assert lib.mf_filter(None, None, 0, None, 0) == mflib.MF_EINVAL
     lib.mf_destroy(None)  # no-op
+
+
+def test_batch_rejects_invalid_descriptions(mflib):
+    lib = mflib.load()
+    lens = (C.c_double * 2)(4.0, 16.0)
+    ok = dict(fs=2048.0, n_det=2, n_samples=1 << 20, f_low=25.0, f_high=1024.0, snr_thr=5.0, window=2048, n_class=2,
+              class_len=lens, max_triggers=1000, cuda_stream=None)
+    for field, value in [("n_det", 0), ("n_det", 9), ("n_class", 0), ("n_class", 9), ("window", 0), ("fs", 0.0),
+                         ("snr_thr", 0.0), ("max_triggers", 0)]:
+        d = mflib.mf_batch_desc(**{**ok, field: value})
+        h = C.c_void_p()
+        assert lib.mf_batch_create(C.byref(h), C.byref(d)) == mflib.MF_EINVAL
+        assert h.value is None
+    bad = (C.c_double * 2)(16.0, 4.0)  # not increasing
+    d = mflib.mf_batch_desc(**{**ok, "class_len": bad})
+    h = C.c_void_p()
+    assert lib.mf_batch_create(C.byref(h), C.byref(d)) == mflib.MF_EINVAL
+    assert lib.mf_batch_run(None, None, 0, 0) == mflib.MF_EINVAL
+    lib.mf_batch_destroy(None)
