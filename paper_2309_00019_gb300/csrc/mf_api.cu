@@ -74,12 +74,6 @@ struct mf_plan_s {
   int64_t* ubc = nullptr;
   int64_t* ucount = nullptr;
   // TMA-staged filter
-  mf::Filter2Maps maps;
-  bool maps_valid = false;
-  int impl = 2;             // 1: per-thread loads, 2: TMA-staged per batch, 3: fused persistent, 4: register-pipelined
-  int fz_B = 1, fz_slots = 3;   // fused schedule: templates per batch, scratch slots
-  unsigned* fz_counters = nullptr;
-  int64_t fz_counters_cap = 0;
   int* status = nullptr;    // device status word
   float2* tw = nullptr;     // sub-FFT twiddle tables [2][1024]
   float2* tw4 = nullptr;    // four-step twiddles w_N^m, m < 32 * N2
@@ -112,12 +106,11 @@ uint64_t plan_fingerprint(const mf_plan_s* p) {
   mix((uint64_t)(uintptr_t)p->row_valid);
   mix((uint64_t)(uintptr_t)p->scratch);
   mix((uint64_t)(uintptr_t)p->slots);
-  mix((uint64_t)p->impl);
   return h;
 }
 
 bool plan_capturable(const mf_plan_s* p) {
-  if (!p || !p->scale_valid || (p->impl != 1 && !p->maps_valid) || p->prof) return false;
+  if (!p || !p->scale_valid || p->prof) return false;
   const int64_t need = (int64_t)p->d.n_det * p->n_tmpl * p->n_win;
   return p->slots_cap >= need && p->sel_cap >= p->n_tmpl && p->bc_cap >= mf::compact_blocks(need);
 }
@@ -197,7 +190,7 @@ mf_status recompute_sigmasq(mf_plan_t p, int64_t row0, int64_t n_rows) {
   p->scale_valid = false;
   if (!p->psd_set || !p->bank || n_rows <= 0) return MF_OK;
   cudaError_t e = mf::launch_sigmasq(p->bank, bank_type(p->bank_dtype), p->ld_bank, p->scales_dev, row0, n_rows,
-                                     p->w_dev, p->nb, p->sigmasq_dev, p->inv_sigma_dev, p->st);
+                                     p->w_dev, p->nb, p->sigmasq_dev, p->inv_sigma_dev, p->st, p->n1, p->n2);
   if (e != cudaSuccess) return cuda_fail(p, e, "sigma^2 kernel");
   return MF_OK;
 }
@@ -291,13 +284,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   int64_t budget = int64_t(256) << 20;
   if (const char* b = std::getenv("MF_SCRATCH_MB")) budget = std::max<int64_t>(1, std::atoll(b)) << 20;
   p->batch = (int)std::max<int64_t>(1, std::min<int64_t>(budget / per, 4096));
-  if (const char* v = std::getenv("MF_FILTER_IMPL")) p->impl = std::atoi(v);
-  if (p->impl < 1 || p->impl > 4) p->impl = 2;
-  if (p->impl == 3 && !mf::fused_supported(d.n)) p->impl = 2;
-  if (const char* v = std::getenv("MF_FUSED_SLOTS")) p->fz_slots = std::max(2, std::atoi(v));
-  p->fz_B = (int)std::max<int64_t>(1, std::min<int64_t>(budget / (per * p->fz_slots), 4096));
-  if (const char* v = std::getenv("MF_FUSED_B")) p->fz_B = std::max(1, std::atoi(v));
-  const int64_t scratch_series = p->impl == 3 ? std::max<int64_t>(p->batch, (int64_t)p->fz_B * p->fz_slots) : p->batch;
+  const int64_t scratch_series = p->batch;
   mf_status s;
   if ((s = dalloc(p, &p->w_dev, p->nb * sizeof(double), "weights")) != MF_OK ||
       (s = dalloc(p, &p->q, (size_t)d.n_det * p->ld_q * sizeof(float2), "weighted data")) != MF_OK ||
@@ -330,7 +317,7 @@ void mf_destroy(mf_plan_t p) {
   dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
   dfree(p->q_lp); dfree(p->dmax); dfree(p->dscale); dfree(p->row_valid);
-  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4); dfree(p->fz_counters);
+  dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
 }
@@ -353,10 +340,9 @@ mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
   if (n_tmpl < 1 || n_tmpl > 0x7fffffff) return fail(p, MF_EINVAL, "mf_bank_reserve: n_tmpl must be in [1, 2^31)");
   cudaStreamSynchronize(p->st);
   p->n_tmpl = 0;
-  p->maps_valid = false;
   p->scale_valid = false;
   p->bank_dtype = dtype;
-  p->ld_bank = (p->nb + 63) / 64 * 64;
+  p->ld_bank = p->d.n / 2;  // column layout of the N/2 bins below Nyquist (launch_to_cols)
   const size_t bytes = (size_t)n_tmpl * p->ld_bank * elem_bytes(dtype);
   mf_status s;
   if ((s = dalloc(p, &p->bank, bytes, "bank")) != MF_OK ||
@@ -396,11 +382,20 @@ mf_status mf_bank_set_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const void
   if (n_rows == 0) return MF_OK;
   const size_t eb = elem_bytes(p->bank_dtype);
   char* dst = (char*)p->bank + (size_t)row0 * p->ld_bank * eb;
-  cudaError_t e = cudaMemcpy2DAsync(dst, p->ld_bank * eb, htilde, ld * eb, p->nb * eb, n_rows,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->st);
+  const void* src = htilde;
+  void* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {  // stage host rows through a temporary device buffer
+    mf_status s = dalloc(p, &tmp, (size_t)n_rows * ld * eb, "bank staging");
+    if (s != MF_OK) return s;
+    e = cudaMemcpyAsync(tmp, htilde, (size_t)n_rows * ld * eb, cudaMemcpyHostToDevice, p->st);
+    src = tmp;
+  }
+  if (e == cudaSuccess) e = mf::launch_to_cols(src, ld, dst, p->ld_bank, n_rows, p->n1, p->n2, (int)eb, p->st);
   if (e == cudaSuccess && scales)
     e = cudaMemcpyAsync(p->scales_dev + row0, scales, n_rows * sizeof(float), cudaMemcpyHostToDevice, p->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_set_rows copy");
   mf_status s = recompute_sigmasq(p, row0, n_rows);
   if (s != MF_OK) return s;
@@ -428,11 +423,21 @@ mf_status mf_bank_quantize_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const
     src = tmp;
   }
   const size_t eb = elem_bytes(p->bank_dtype);
+  void* q16 = nullptr;  // quantised rows in natural layout, then into the bank's column layout
+  if (e == cudaSuccess) {
+    mf_status s = dalloc(p, &q16, (size_t)n_rows * p->nb * eb, "quantised rows");
+    if (s != MF_OK) {
+      dfree(tmp);
+      return s;
+    }
+    e = mf::launch_quant_bank(src, ld, n_rows, p->nb, bank_type(p->bank_dtype), q16, p->nb, p->scales_dev + row0, p->st);
+  }
   if (e == cudaSuccess)
-    e = mf::launch_quant_bank(src, ld, n_rows, p->nb, bank_type(p->bank_dtype), (char*)p->bank + (size_t)row0 * p->ld_bank * eb,
-                              p->ld_bank, p->scales_dev + row0, p->st);
+    e = mf::launch_to_cols(q16, p->nb, (char*)p->bank + (size_t)row0 * p->ld_bank * eb, p->ld_bank, n_rows, p->n1, p->n2,
+                           (int)eb, p->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
   dfree(tmp);
+  if (q16) cudaFree(q16);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_bank_quantize_rows");
   mf_status s = recompute_sigmasq(p, row0, n_rows);
   if (s != MF_OK) return s;
@@ -453,10 +458,8 @@ mf_status mf_set_data_dtype(mf_plan_t p, mf_dtype dtype) {
     cudaError_t e = cudaMemsetAsync(p->q_lp, 0, (size_t)p->d.n_det * p->ld_q * 4, p->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_data_dtype");
-    p->impl = 2;
   }
   p->data_dtype = dtype;
-  p->maps_valid = false;
   return MF_OK;
 }
 
@@ -478,7 +481,6 @@ mf_status mf_set_row_valid(mf_plan_t p, const int64_t* range) {
   cudaError_t e = cudaMemcpyAsync(p->row_valid, r.data(), r.size() * sizeof(int2), cudaMemcpyHostToDevice, p->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_set_row_valid");
-  p->impl = 2;
   return MF_OK;
 }
 
@@ -487,7 +489,7 @@ mf_status mf_set_batch(mf_plan_t p, int32_t batch) {
   if (batch < 1) return fail(p, MF_EINVAL, "mf_set_batch: batch must be >= 1");
   cudaStreamSynchronize(p->st);
   const int64_t per = (int64_t)p->d.n_det * p->d.n * (int64_t)sizeof(float2);
-  const int64_t series = p->impl == 3 ? std::max<int64_t>(batch, (int64_t)p->fz_B * p->fz_slots) : batch;
+  const int64_t series = batch;
   mf_status s = dalloc(p, &p->scratch, (size_t)series * per, "scratch");
   if (s != MF_OK) return s;
   p->batch = batch;
@@ -551,11 +553,12 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter selection copy");
   const int64_t n_slots = (int64_t)p->d.n_det * n_sel * p->n_win;
   const int64_t launches_before = mf::launch_count();
-  e = mf::launch_prep((const float2*)dtilde, ld_dtilde, p->w_dev, p->nb, p->d.n_det, p->q, p->ld_q, p->slots, n_slots,
-                      p->st, 1.0 / p->sigma_ref);
+  e = mf::launch_prep_cols((const float2*)dtilde, ld_dtilde, p->w_dev, p->n1, p->n2, p->d.n_det, p->q, p->ld_q,
+                           p->slots, n_slots, p->st, 1.0 / p->sigma_ref);
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter prep");
   if (p->data_dtype != MF_F32) {
-    e = mf::launch_quant_q(p->q, p->ld_q, p->nb, p->d.n_det, bank_type(p->data_dtype), p->q_lp, p->dmax, p->dscale, p->st);
+    e = mf::launch_quant_q(p->q, p->ld_q, p->d.n / 2, p->d.n_det, bank_type(p->data_dtype), p->q_lp, p->dmax, p->dscale,
+                           p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter data quantisation");
   }
   mf::FilterArgs a{};
@@ -590,72 +593,19 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.q_type = bank_type(p->data_dtype);
   a.q_lp = p->q_lp;
   a.dscale = p->dscale;
-  if (p->impl != 1 && !p->maps_valid) {
-    e = mf::filter2_encode_maps(a, p->n_tmpl, &p->maps);
-    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter tensor maps");
-    p->maps_valid = true;
-  }
   LaunchScope ls(p);
   ls.before = launches_before;
-  if (p->impl == 3 && n_sel > 0) {
-    // one persistent launch for every batch and both passes
-    mf::FusedSched q{};
-    q.B = p->fz_B;
-    q.nb = (int)((n_sel + q.B - 1) / q.B);
-    q.n_slots = p->fz_slots;
-    q.n_det = p->d.n_det;
-    int i1 = 0, i2 = 0;
-    mf::fused_items(p->d.n, &i1, &i2);
-    const int64_t last = n_sel - (int64_t)(q.nb - 1) * q.B;
-    q.F1 = q.B * q.n_det * i1;
-    q.F2 = q.B * q.n_det * i2;
-    q.L1 = (int)last * q.n_det * i1;
-    q.L2 = (int)last * q.n_det * i2;
-    const int64_t total = (int64_t)(q.nb - 1) * (q.F1 + q.F2) + q.L1 + q.L2;
-    if (total > 0x7fffffff) return fail(p, MF_EINVAL, "mf_filter: selection too large for one launch");
-    q.total = (int)total;
-    const int64_t need = 1 + 2 * (int64_t)q.nb;
-    if (need > p->fz_counters_cap) {
-      mf_status s2 = dalloc(p, &p->fz_counters, (size_t)need * sizeof(unsigned), "fused counters");
-      if (s2 != MF_OK) {
-        p->fz_counters_cap = 0;
-        return s2;
-      }
-      p->fz_counters_cap = need;
-    }
-    e = cudaMemsetAsync(p->fz_counters, 0, need * sizeof(unsigned), p->st);
-    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter counters");
-    q.head = p->fz_counters;
-    q.done1 = p->fz_counters + 1;
-    q.done2 = p->fz_counters + 1 + q.nb;
-    a.pos0 = 0;
-    a.count = (int)std::min<int64_t>(n_sel, 0x7fffffff);
-    const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
-    const int e0 = prof ? (int)p->samples.size() * 3 : 0;
-    if (prof) cudaEventRecord(p->ev[e0], p->st);
-    e = mf::launch_filter_fused(a, p->maps, q, p->st);
-    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter fused kernel");
-    if (prof) {
-      cudaEventRecord(p->ev[e0 + 1], p->st);
-      cudaEventRecord(p->ev[e0 + 2], p->st);
-      p->samples.push_back({e0, -n_sel * p->d.n_det});  // negative: one fused launch covering both passes
-    }
-  }
-  for (int64_t pos0 = 0; p->impl != 3 && pos0 < n_sel; pos0 += p->batch) {
+  for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
     a.pos0 = pos0;
     a.first_batch = pos0 == 0 ? 1 : 0;
     a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
     const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
     const int e0 = prof ? (int)p->samples.size() * 3 : 0;
     if (prof) cudaEventRecord(p->ev[e0], p->st);
-    e = p->impl == 1   ? mf::launch_filter_pass1(a, p->st)
-        : p->impl == 4 ? mf::launch_filter4_pass1(a, p->st)
-                       : mf::launch_filter2_pass1(a, p->maps, p->st);
+    e = mf::launch_filter2_pass1(a, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 1");
     if (prof) cudaEventRecord(p->ev[e0 + 1], p->st);
-    e = p->impl == 1   ? mf::launch_filter_pass2(a, p->st)
-        : p->impl == 4 ? mf::launch_filter4_pass2(a, p->st)
-                       : mf::launch_filter2_pass2(a, p->st);
+    e = mf::launch_filter2_pass2(a, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 2");
     if (prof) {
       cudaEventRecord(p->ev[e0 + 2], p->st);
@@ -693,12 +643,6 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     e = cudaEventElapsedTime(&t1, p->ev[sm.e0], p->ev[sm.e0 + 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, p->ev[sm.e0 + 1], p->ev[sm.e0 + 2]);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_stats elapsed");
-    if (sm.series < 0) {  // fused launch: both passes in one kernel
-      p->stats.fused_launches += 1;
-      p->stats.fused_series += -sm.series;
-      p->stats.fused_ms += t1;
-      continue;
-    }
     p->stats.pass1_launches += 1;
     p->stats.pass1_series += sm.series;
     p->stats.pass1_ms += t1;
@@ -707,8 +651,8 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     p->stats.pass2_ms += t2;
   }
   p->samples.clear();
-  p->stats.impl = p->impl;
-  p->stats.batch = p->impl == 3 ? p->fz_B : p->batch;
+  p->stats.impl = 2;
+  p->stats.batch = p->batch;
   *out = p->stats;
   if (reset) p->stats = mf_plan_stats{};
   return MF_OK;

@@ -62,13 +62,6 @@ struct FilterArgs {
   const int2* row_valid;
 };
 
-// Tensor maps of the TMA-staged filter: template bank and weighted data, each
-// viewed as [depth][N1/2 rows k1][N2 columns k2].
-struct Filter2Maps {
-  CUtensorMap h;
-  CUtensorMap q;
-  bool ok = false;
-};
 // Quantise the FP32 weighted data q [n_det][ld_q] (nb bins per detector) to
 // 16-bit (q_type) q_lp with a per-detector power-of-two scale c_d chosen so that
 // max |c_d q| is in [2^14, 2^15); writes dscale[d] = c_d.  dmax: n_det words of
@@ -87,32 +80,24 @@ cudaError_t launch_quant_bank(const float2* src, int64_t ld_src, int64_t n_rows,
 int64_t plan_templates(const ::mf_plan_s* p);
 uint64_t plan_fingerprint(const ::mf_plan_s* p);
 bool plan_capturable(const ::mf_plan_s* p);
-cudaError_t filter2_encode_maps(const FilterArgs& a, int64_t n_tmpl, Filter2Maps* m);
-cudaError_t launch_filter2_pass1(const FilterArgs& a, const Filter2Maps& m, cudaStream_t st);
+// The TMA-staged filter passes (mf_filter.cu).  The bank rows and the
+// weighted data are in column layout: element k = k1 N2 + k2 of the non-zero
+// half (k1 < N1/2) at k2 N1/2 + k1 (see launch_to_cols).
+cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);
-// register-pipelined variant of the two passes (direct loads, no staging)
-cudaError_t launch_filter4_pass1(const FilterArgs& a, cudaStream_t st);
-cudaError_t launch_filter4_pass2(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st);
 // w_N^m for m < count (count <= 32768)
 cudaError_t launch_fill_tw4(int64_t n, float2* tw4, int64_t count, cudaStream_t st);
 
-// Schedule of the fused persistent filter (both passes of every batch in one
-// launch).  The selection is cut into nb batches of B templates (the last one
-// may be short); F1/F2 (L1/L2) are the pass-1/pass-2 items of a full (the
-// last) batch; scratch holds n_slots batches; head/done1/done2 are zeroed
-// device counters (done1/done2 of length nb).
-struct FusedSched {
-  int B, nb, n_slots, n_det;
-  int F1, F2, L1, L2;
-  int total;
-  unsigned* head;
-  unsigned* done1;
-  unsigned* done2;
-};
-bool fused_supported(int64_t n);
-void fused_items(int64_t n, int* p1_per_series, int* p2_per_series);
-cudaError_t launch_filter_fused(const FilterArgs& a, const Filter2Maps& m, const FusedSched& q, cudaStream_t st);
+// Column layout of spectra rows: dst[r][k2 N1/2 + k1] = src[r][k1 N2 + k2] for
+// k1 < N1/2, k2 < N2 (the bins k < N/2), elem_bytes 8 (complex64) or 4 (16-bit
+// pairs); src rows ld_src elements apart, dst rows ld_dst.
+cudaError_t launch_to_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t n_rows, int n1, int n2,
+                           int elem_bytes, cudaStream_t st);
+// q = q_scale w s~ in column layout (q [n_det][ld_q], N/2 elements per row)
+cudaError_t launch_prep_cols(const float2* dtilde, int64_t ld_d, const double* w, int n1, int n2, int n_det,
+                             float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st,
+                             double q_scale);
 
 // Message returned by mf_last_error(NULL) for calls without a plan.
 void set_global_error(const char* msg);
@@ -132,9 +117,11 @@ cudaError_t launch_filter_batch(const FilterArgs& a, cudaStream_t st);
 // the two halves of launch_filter_batch, for per-kernel timing
 cudaError_t launch_filter_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter_pass2(const FilterArgs& a, cudaStream_t st);
+// sigma^2 of bank rows [row0, row0 + n_rows) in natural layout (n1 = 0: bins
+// 0..nb-1) or column layout (n1, n2 > 0: the N/2 bins of launch_to_cols)
 cudaError_t launch_sigmasq(const void* bank, int bank_type, int64_t ld_bank, const float* scales,
                            int64_t row0, int64_t n_rows, const double* w, int64_t nb,
-                           double* sigmasq, float* inv_sigma, cudaStream_t st);
+                           double* sigmasq, float* inv_sigma, cudaStream_t st, int n1 = 0, int n2 = 0);
 // compaction of window maxima into mf_trigger records (layout of the public struct)
 cudaError_t launch_compact(const unsigned long long* slots, int n_det, int64_t n_sel, int64_t n_win,
                            int64_t window, const int32_t* sel, void* trig_out, int64_t trig_cap,

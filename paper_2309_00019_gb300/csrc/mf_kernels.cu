@@ -335,15 +335,21 @@ __global__ void k_zero_u64(unsigned long long* p, int64_t n) {
     p[i] = 0ull;
 }
 
+// n1 = 0: row t holds bins 0..nb-1; n1 > 0: column layout (stored index
+// i = k2 n1/2 + k1 holds bin k = k1 n2 + k2, i < N/2)
 template <int BT>
 __global__ void k_sigmasq(const void* bank, int64_t ld_bank, const float* scales, int64_t row0,
-                          const double* __restrict__ w, int64_t nb, double* sigmasq, float* inv_sigma) {
+                          const double* __restrict__ w, int64_t nb, double* sigmasq, float* inv_sigma, int n1,
+                          int n2) {
   const int64_t t = row0 + blockIdx.x;
   double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
+  const int64_t count = n1 > 0 ? (int64_t)n1 * n2 / 2 : nb;
+  const int R = n1 / 2;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const int64_t k = n1 > 0 ? (int64_t)(i % R) * n2 + i / R : i;
     const double wk = w[k];
     if (wk != 0.0) {
-      const float2 h = BankElem<BT>::get(bank, t * ld_bank + k);
+      const float2 h = BankElem<BT>::get(bank, t * ld_bank + i);
       acc += wk * ((double)h.x * h.x + (double)h.y * h.y);
     }
   }
@@ -486,6 +492,40 @@ __global__ void k_compact_write(const unsigned long long* __restrict__ slots, in
   }
 }
 
+
+// --- column layout of spectra (the filter's bank and weighted-data layout) ----
+
+// dst[r][k2 R + k1] = src[r][k1 n2 + k2], k1 < R = n1/2, k2 < n2: 32 x 32 tiles
+// through shared memory, coalesced on both sides.  grid (n2/32, R/32, rows).
+template <typename E>
+__global__ void k_to_cols(const E* __restrict__ src, int64_t ld_src, E* __restrict__ dst, int64_t ld_dst, int n1,
+                          int n2, int64_t row0) {
+  __shared__ E tile[32][33];
+  const int R = n1 / 2;
+  const int64_t row = row0 + blockIdx.z;
+  const int k1_0 = blockIdx.y * 32, k2_0 = blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y)
+    tile[y][threadIdx.x] = src[row * ld_src + (int64_t)(k1_0 + y) * n2 + k2_0 + threadIdx.x];
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y)
+    dst[row * ld_dst + (int64_t)(k2_0 + y) * R + k1_0 + threadIdx.x] = tile[threadIdx.x][y];
+}
+
+// q[det][k2 R + k1] = q_scale w[k] s~[det][k], k = k1 n2 + k2 (FP64 product)
+__global__ void k_prep_cols(const float2* __restrict__ d, int64_t ld_d, const double* __restrict__ w, int n1, int n2,
+                            int n_det, float2* __restrict__ q, int64_t ld_q, double q_scale) {
+  const int R = n1 / 2;
+  const int64_t half = (int64_t)R * n2;
+  const int64_t total = half * n_det;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int det = (int)(i / half);
+    const int64_t ii = i - (int64_t)det * half;
+    const int64_t k = (ii % R) * n2 + ii / R;
+    const double wk = w[k] * q_scale;
+    const float2 s = d[(int64_t)det * ld_d + k];
+    q[(int64_t)det * ld_q + ii] = make_float2((float)(wk * (double)s.x), (float)(wk * (double)s.y));
+  }
+}
 
 // --- 16-bit storage (bank and weighted data) ---------------------------------
 
@@ -639,20 +679,53 @@ cudaError_t launch_quant_bank(const float2* src, int64_t ld_src, int64_t n_rows,
   return cudaGetLastError();
 }
 
+cudaError_t launch_to_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t n_rows, int n1, int n2,
+                           int elem_bytes, cudaStream_t st) {
+  if (n1 < 64 || n2 < 32 || (elem_bytes != 8 && elem_bytes != 4)) return cudaErrorInvalidValue;
+  for (int64_t r0 = 0; r0 < n_rows; r0 += 65535) {
+    const dim3 g((unsigned)(n2 / 32), (unsigned)(n1 / 2 / 32), (unsigned)std::min<int64_t>(65535, n_rows - r0));
+    const dim3 b(32, 8);
+    if (elem_bytes == 8)
+      k_to_cols<float2><<<g, b, 0, st>>>(static_cast<const float2*>(src), ld_src, static_cast<float2*>(dst), ld_dst,
+                                         n1, n2, r0);
+    else
+      k_to_cols<uint32_t><<<g, b, 0, st>>>(static_cast<const uint32_t*>(src), ld_src, static_cast<uint32_t*>(dst),
+                                           ld_dst, n1, n2, r0);
+    ++g_launches;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_cols(const float2* dtilde, int64_t ld_d, const double* w, int n1, int n2, int n_det,
+                             float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st,
+                             double q_scale) {
+  const int g = num_sms() * 4;
+  k_prep_cols<<<g, 256, 0, st>>>(dtilde, ld_d, w, n1, n2, n_det, q, ld_q, q_scale);
+  ++g_launches;
+  if (slots && n_slots > 0) {
+    k_zero_u64<<<g, 256, 0, st>>>(slots, n_slots);
+    ++g_launches;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sigmasq(const void* bank, int bank_type, int64_t ld_bank, const float* scales, int64_t row0,
                            int64_t n_rows, const double* w, int64_t nb, double* sigmasq, float* inv_sigma,
-                           cudaStream_t st) {
+                           cudaStream_t st, int n1, int n2) {
   if (n_rows <= 0) return cudaSuccess;
   if (n_rows > 0x7fffffff) return cudaErrorInvalidValue;
   switch (bank_type) {
     case kBankF32:
-      k_sigmasq<kBankF32><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      k_sigmasq<kBankF32><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma,
+                                                             n1, n2);
       break;
     case kBankF16:
-      k_sigmasq<kBankF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      k_sigmasq<kBankF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma,
+                                                             n1, n2);
       break;
     case kBankBF16:
-      k_sigmasq<kBankBF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma);
+      k_sigmasq<kBankBF16><<<(unsigned)n_rows, 256, 0, st>>>(bank, ld_bank, scales, row0, w, nb, sigmasq, inv_sigma,
+                                                             n1, n2);
       break;
     default:
       return cudaErrorInvalidValue;
