@@ -39,8 +39,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
-KERNEL_NAMES = {1: ("k_pass1", "k_pass2"), 2: ("k_cols", "k_rows"), 3: ("k_fused", "k_fused"),
-                4: ("k_cols4", "k_rows4")}
+KERNEL_NAMES = {2: ("k_cols", "k_rows")}
 
 
 def measured_traffic(kernel, series_per_launch):
@@ -206,10 +205,8 @@ def oracle_sample_rate(cfg, budget_s, n_each=None):
 # ---------------------------------------------------------------------------
 
 def dist_setup(args):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2309_00019_gb300.multi import rank_env
+    return rank_env()
 
 
 def reference_arm(args, rank, world):
@@ -253,6 +250,7 @@ def main():
     import synth
     from paper_2309_00019_gb300 import _build, mf
     from paper_2309_00019_gb300.hierarchy import HierParams, Hierarchy
+    from paper_2309_00019_gb300.multi import reduce_timing, segment_seed
 
     if not os.path.exists(mf.LIB_PATH):
         _build.build()
@@ -264,7 +262,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    cfg = synth.make_config2(seed=1 + rank, small=args.small)
+    cfg = synth.make_config2(seed=segment_seed(1, rank), small=args.small)
     hp = HierParams.from_config(cfg)
     h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), cfg.nbhd_ptr, cfg.nbhd_idx,
                   device=dev)
@@ -318,12 +316,7 @@ def main():
         p.profile(False)
     t_dev = sum(step_ms) / 1e3
     if dist is not None:
-        tt = torch.tensor([t_dev, td_total], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        t_max, td_all = float(mx[0]), float(sm[1])
+        t_max, td_all = reduce_timing(dist, t_dev, td_total, dev)
     else:
         t_max, td_all = t_dev, td_total
     value = td_all / t_max
@@ -335,10 +328,6 @@ def main():
         n1s, n2s = 1 << ((lg + 1) // 2), 1 << (lg // 2)
         names = KERNEL_NAMES.get(s["impl"], ("pass1", "pass2"))
         nb = n // 2 + 1
-        if s["fused_launches"] > 0:
-            kinds.append(dict(kernel=f"k_fused<{n1s}> ({stage})", ms=s["fused_ms"], launches=s["fused_launches"],
-                              series=s["fused_series"], flops_series=5.0 * n * math.log2(n), n=n,
-                              tmpl_bytes_series=nb * 8 / hp.n_det))
         for k, sub, nm in (("pass1", n1s, names[0]), ("pass2", n2s, names[1])):
             if s[f"{k}_launches"] > 0:
                 kinds.append(dict(kernel=f"{nm}<{n1s},{n2s}> ({stage})", ms=s[f"{k}_ms"],
@@ -389,12 +378,8 @@ def main():
             d2h += trig2.nbytes + co.nbytes + 16
         e_val = td_e / sum(te)
         if dist is not None:
-            tt = torch.tensor([sum(te), td_e], dtype=torch.float64, device=dev)
-            mx = tt.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            sm_ = tt.clone()
-            dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-            e_val = float(sm_[1]) / float(mx[0])
+            t_e, td_e_all = reduce_timing(dist, sum(te), td_e, dev)
+            e_val = td_e_all / t_e
         e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(cfg.strain.nbytes),
                "d2h_bytes_per_step": int(d2h / args.steps)}
 

@@ -206,6 +206,17 @@ mf_status mf_profile(mf_plan_t plan, int enable);
  * zeroes them afterwards. */
 mf_status mf_get_stats(mf_plan_t plan, mf_plan_stats* out, int reset);
 
+/* Failure detection without a GPU fault (no counterpart in the paper): every
+ * device wait in the filter kernels is bounded; on expiry it records a timeout
+ * in the plan's status word, the kernel returns, and the next mf_get_triggers
+ * returns MF_ETIMEOUT (clearing the word).  This call exercises that path: it
+ * launches, on the plan's stream, one CTA of 128 threads that wait on a
+ * barrier nothing completes, so each wait gives up after about 2^31 cycles
+ * (about 1 s) and records the timeout.  *returned = threads that came back
+ * (128 when the mechanism works).  The context stays usable.  Synchronises.
+ * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+mf_status mf_selftest_wait(mf_plan_t plan, int32_t* returned);
+
 /* ---- two-detector coincidence and follow-up (Sec. III) ---------------- */
 
 typedef struct {

@@ -684,6 +684,22 @@ mf_status mf_get_triggers(mf_plan_t p, mf_trigger* out, int64_t cap, int64_t* n_
   return MF_OK;
 }
 
+mf_status mf_selftest_wait(mf_plan_t p, int32_t* returned) {
+  if (!p || !returned) return fail(p, MF_EINVAL, "mf_selftest_wait: null argument");
+  int* cnt = nullptr;
+  mf_status s = dalloc(p, &cnt, sizeof(int), "self-test counter");
+  if (s != MF_OK) return s;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int), p->st);
+  if (e == cudaSuccess) e = mf::launch_wait_selftest(p->status, cnt, p->st);
+  int r = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r, cnt, sizeof(int), cudaMemcpyDeviceToHost, p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_selftest_wait");
+  *returned = r;
+  return MF_OK;
+}
+
 mf_status mf_device_triggers(mf_plan_t p, const mf_trigger** trig, const int64_t** count) {
   if (!p || !trig || !count) return fail(p, MF_EINVAL, "mf_device_triggers: null argument");
   if (!p->filtered) return fail(p, MF_ESTATE, "mf_device_triggers: no filter run");

@@ -99,6 +99,10 @@ cudaError_t launch_prep_cols(const float2* dtilde, int64_t ld_d, const double* w
                              float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st,
                              double q_scale);
 
+// One CTA of 128 threads waiting on a barrier nothing completes (bounded waits
+// record a timeout in *status; *returned counts the threads that returned).
+cudaError_t launch_wait_selftest(int* status, int* returned, cudaStream_t st);
+
 // Message returned by mf_last_error(NULL) for calls without a plan.
 void set_global_error(const char* msg);
 inline void set_global_error(const std::string& msg) { set_global_error(msg.c_str()); }

@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include "mf_common.cuh"
+#include "mf_tma.cuh"
 
 namespace mf {
 
@@ -493,6 +494,21 @@ __global__ void k_compact_write(const unsigned long long* __restrict__ slots, in
 }
 
 
+// --- failure detection without a fault ----------------------------------------
+
+// One CTA waits on an mbarrier that no thread and no copy ever completes: every
+// thread's bounded wait gives up after ~2^31 cycles, records kStatusTimeout in
+// *status and returns; *returned counts the threads that came back.
+__global__ void k_wait_selftest(int* status, int* returned) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0, status)) atomicAdd(returned, 1);
+}
+
 // --- column layout of spectra (the filter's bank and weighted-data layout) ----
 
 // dst[r][k2 R + k1] = src[r][k1 n2 + k2], k1 < R = n1/2, k2 < n2: 32 x 32 tiles
@@ -609,6 +625,12 @@ __global__ void k_quant_bank(const float2* __restrict__ src, int64_t ld_src, int
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_wait_selftest(int* status, int* returned, cudaStream_t st) {
+  k_wait_selftest<<<1, 128, 0, st>>>(status, returned);
+  ++g_launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tmpl_scale(const float* inv_sigma, int64_t n_tmpl, double sigma_ref, double thr2, float* ratio,
                               float* thr_raw, cudaStream_t st) {

@@ -88,6 +88,7 @@ SIGNATURES = {
     "mf_bank_quantize_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, C.c_int]),
     "mf_set_data_dtype": (C.c_int, [_P, C.c_int]),
     "mf_set_row_valid": (C.c_int, [_P, _P]),
+    "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mf_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(mf_batch_desc)]),
     "mf_batch_destroy": (None, [_P]),
     "mf_batch_last_error": (C.c_char_p, [_P]),
@@ -244,6 +245,12 @@ class Plan:
         """Per-row analysed ranges, int64 [n_det, 2] (None restores the plan's range)."""
         r = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
         _check(self.h, self.lib.mf_set_row_valid(self.h, _ptr(r)))
+
+    def selftest_wait(self):
+        """Run the bounded-wait self-test; returns the number of threads that came back."""
+        r = C.c_int32(0)
+        _check(self.h, self.lib.mf_selftest_wait(self.h, C.byref(r)))
+        return r.value
 
     def set_batch(self, batch):
         _check(self.h, self.lib.mf_set_batch(self.h, batch))

@@ -190,3 +190,23 @@ def test_errors_are_reported_not_raised_in_c(mf):
     assert lib.mf_filter(p.h, dt.data_ptr(), 2049, None, 3) == mf.MF_EINVAL  # null subset with a count
     with pytest.raises(mf.MFError):
         p.load_bank(np.zeros((1, 2049), np.complex64), dtype=mf.MF_F16)  # 16-bit bank without scales
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable(mf):
+    """Failure detection without a fault: a wait that nothing completes gives up,
+    every waiting thread returns, the plan reports MF_ETIMEOUT once, and the
+    next filter gives the same triggers as before."""
+    c = synth.make_config1()
+    p = _plan(mf, c.fs, c.n, 1, c.f_low, c.thr, c.window)
+    p.set_psd(c.psd)
+    p.load_bank(torch.from_numpy(c.bank()).to(DEV))
+    sfd = torch.from_numpy((c.noise_fd + c.signal_fd).astype(np.complex64)[None, :]).to(DEV)
+    p.filter(sfd)
+    ref, _, _ = p.triggers()
+    assert p.selftest_wait() == 128
+    with pytest.raises(mf.MFError) as e:
+        p.triggers()
+    assert e.value.status == mf.MF_ETIMEOUT
+    p.filter(sfd)
+    got, _, _ = p.triggers()
+    assert np.array_equal(got, ref)
