@@ -168,6 +168,53 @@ def filter_bank(stilde, bank, psd, n, fs, f_low, f_high, thr, window,
 
 
 # ---------------------------------------------------------------------------
+# signal-based veto at trigger times: chi^2_r and the re-weighted SNR (Eq. 4)
+# ---------------------------------------------------------------------------
+
+def chisq_bins(htilde, w, p):
+    """Band edges of the chi^2 test: p contiguous bands of the analysis band,
+    each holding ~1/p of the template power sigma^2 = sum w |h|^2.  Bin k goes
+    to band floor(p C(k) / sigma^2), with C(k) the template power of the bins
+    below k (reading; the paper cites the test, Eq. 4, without its bands).
+    Returns an int array [N/2+1] of band indices (-1 outside the band)."""
+    h = np.asarray(htilde, dtype=np.complex128)
+    pw = w * (h.real ** 2 + h.imag ** 2)
+    s2 = pw.sum()
+    below = np.concatenate([[0.0], np.cumsum(pw)[:-1]])
+    band = np.minimum(np.floor(p * below / s2).astype(np.int64), p - 1)
+    band[w == 0] = -1
+    return band
+
+
+def chisq(stilde, htilde, w, n, sample, p):
+    """Allen's chi^2 at one sample: the complex filter output z split by band,
+    z_l = sum_{k in band l} w s~ h~* e^{+2 pi i k j / N}, and
+    chi^2 = p sum_l |z_l - z / p|^2 / sigma^2 (2p - 2 degrees of freedom
+    in Gaussian noise).  Returns chi^2."""
+    h = np.asarray(htilde, dtype=np.complex128)
+    s = np.asarray(stilde, dtype=np.complex128)
+    band = chisq_bins(h, w, p)
+    k = np.arange(len(h))
+    terms = w * s * np.conj(h) * np.exp(2j * math.pi * k * int(sample) / n)
+    z_l = np.array([terms[band == l].sum() for l in range(p)])
+    z = z_l.sum()
+    s2 = sigmasq(h, w)
+    return float(p * np.sum(np.abs(z_l - z / p) ** 2) / s2)
+
+
+def reduced_chisq(chi2, p):
+    """chi^2_r = chi^2 / (2p - 2)."""
+    return chi2 / (2 * p - 2)
+
+
+def newsnr(rho, chi2_r):
+    """Eq. (4): rho / [(1 + chi2_r^3) / 2]^(1/6) when chi2_r >= 1, else rho."""
+    rho = np.asarray(rho, dtype=np.float64)
+    c = np.asarray(chi2_r, dtype=np.float64)
+    return np.where(c >= 1.0, rho / ((1.0 + c ** 3) / 2.0) ** (1.0 / 6.0), rho)
+
+
+# ---------------------------------------------------------------------------
 # overlapping segments of long data (Sec. V.C)
 # ---------------------------------------------------------------------------
 

@@ -34,3 +34,22 @@ def reduce_timing(dist, seconds, work, device=None):
     sm = t.clone()
     dist.all_reduce(sm, op=dist.ReduceOp.SUM)
     return float(mx[0]), float(sm[1])
+
+
+def merge_triggers(parts):
+    """Trigger lists of template-range shards, each ordered by (det, tmpl,
+    sample), merged into the order of the unsharded run."""
+    import numpy as np
+
+    parts = [p for p in parts if p is not None and len(p)]
+    if not parts:
+        return None
+    return np.sort(np.concatenate(parts), order=["det", "tmpl", "sample"], kind="stable")
+
+
+def gather_triggers(dist, trig):
+    """Variable-size gather of every rank's trigger list, merged (every rank
+    gets the merge): the one collective a bank sharded by template range needs."""
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, trig)
+    return merge_triggers(parts)
