@@ -313,6 +313,39 @@ def followed_up(coincs, rho_c_thr):
     return np.unique(coincs["tmpl"][sel]).astype(np.int32)
 
 
+def background_count(stat_bg, x, scale=1.0):
+    """n_b(x): background coincidences with statistic >= x, times scale (the
+    ratio of background volumes, Sec. IV: the hierarchical background is
+    scaled by the ratio of time-shift intervals)."""
+    bg = np.sort(np.asarray(stat_bg, dtype=np.float64))
+    x = np.asarray(x, dtype=np.float64)
+    return scale * (len(bg) - np.searchsorted(bg, x, side="left"))
+
+
+def far_count(stat_fg, stat_bg, t_bg, scale=1.0):
+    """Eq. (6): FAR = (1 + n_b(Lambda_b >= Lambda_f)) / T_b for each foreground value."""
+    return (1.0 + background_count(stat_bg, stat_fg, scale)) / float(t_bg)
+
+
+def tail_fit(stat_bg, fit_min, scale=1.0):
+    """Sec. IV: least-squares line log n_b = alpha + beta Lambda through the
+    cumulative background counts at every background value >= fit_min
+    (natural logarithm; n_b scaled as in background_count).  Returns (alpha, beta)."""
+    bg = np.sort(np.asarray(stat_bg, dtype=np.float64))
+    x = bg[bg >= fit_min]
+    if len(x) < 2:
+        raise ValueError("fewer than two background values above fit_min")
+    y = np.log(background_count(bg, x, scale))
+    A = np.stack([np.ones_like(x), x], axis=1)
+    (alpha, beta), *_ = np.linalg.lstsq(A, y, rcond=None)
+    return float(alpha), float(beta)
+
+
+def far_fit(stat_fg, alpha, beta, t_bg):
+    """Eq. (6) with the fitted background: (1 + exp(alpha + beta Lambda_f)) / T_b."""
+    return (1.0 + np.exp(alpha + beta * np.asarray(stat_fg, dtype=np.float64))) / float(t_bg)
+
+
 def nbhd_union(coarse_ids, ptr, idx):
     """Union of the neighbourhoods of the followed-up coarse templates (Sec. III),
     as sorted unique fine-template ids."""
