@@ -206,6 +206,23 @@ mf_status mf_profile(mf_plan_t plan, int enable);
  * zeroes them afterwards. */
 mf_status mf_get_stats(mf_plan_t plan, mf_plan_stats* out, int reset);
 
+/* Signal-based veto at the triggers of the last mf_filter (Sec. II: triggers
+ * are down-weighted by their chi^2; the re-weighted SNR is Eq. 4).  For each
+ * trigger (det, tmpl, sample) of the device trigger list (mf_device_triggers
+ * order, the first min(count, max_triggers)), with z the filter output at
+ * the sample split over n_bands frequency bands of equal template power
+ * (band l = bins k with floor(n_bands C(k) / sigma^2) = l, C(k) = the
+ * template power sum_{k' < k} w |h~|^2 below k; the paper cites the test
+ * without its bands, this is the reading):
+ *   chi2[i]   = n_bands sum_l |z_l - z / n_bands|^2 / sigma^2  (2 n_bands - 2 dof),
+ *   newsnr[i] = rho / [(1 + c^3) / 2]^{1/6} with c = chi2 / (2 n_bands - 2) if
+ *               c >= 1, else rho  (Eq. 4).
+ * chi2, newsnr: device float32 [max_triggers].  The band edges are computed
+ * on the first call for a bank, PSD and n_bands (FP64).  Asynchronous on the
+ * plan's stream.  Errors: MF_EINVAL (n_bands not in [2, 64]), MF_ESTATE (no
+ * filter run), MF_ENOMEM. */
+mf_status mf_chisq(mf_plan_t plan, int32_t n_bands, float* chi2, float* newsnr);
+
 /* Failure detection without a GPU fault (no counterpart in the paper): every
  * device wait in the filter kernels is bounded; on expiry it records a timeout
  * in the plan's status word, the kernel returns, and the next mf_get_triggers
@@ -250,6 +267,22 @@ mf_status mf_coincide(mf_plan_t plan, const mf_coinc_desc* desc, int32_t* follow
  * sample0, sample1), into host out[cap].  Synchronises.  MF_EOVERFLOW as for
  * triggers. */
 mf_status mf_get_coincs(mf_plan_t plan, mf_coinc* out, int64_t cap, int64_t* n_found);
+
+/* Background estimate from time-shifted coincidences (Sec. IV, Eq. 6).  For
+ * each foreground statistic stat_fg[i] (host float32 [n_fg], e.g. rho_c of the
+ * zero-lag coincidences) against the background stat_bg (host float32
+ * [n_bg], the shifted coincidences), with n_b(x) = scale x #{bg >= x}
+ * (scale: ratio of background volumes, Sec. IV):
+ *   far_count[i] = (1 + n_b(stat_fg[i])) / t_bg                 (Eq. 6),
+ *   far_fit[i]   = (1 + exp(alpha + beta stat_fg[i])) / t_bg,
+ * where log n_b = alpha + beta x is the least-squares line through the
+ * cumulative counts at every background value >= fit_min (natural log; the
+ * Sec. IV tail fit).  t_bg: background time, s (> 0).  Outputs are host
+ * float64 (far_fit, alpha, beta may be NULL; they are NaN when fewer than two
+ * background values reach fit_min).  Host computation, no device work.
+ * Errors: MF_EINVAL. */
+mf_status mf_far(const float* stat_fg, int64_t n_fg, const float* stat_bg, int64_t n_bg, double t_bg, double scale,
+                 double fit_min, double* far_count, double* far_fit, double* alpha, double* beta);
 
 /* Neighbourhood map coarse -> fine (CSR: ptr int64 [n_coarse+1], idx int32
  * [ptr[n_coarse]] fine template ids of this plan's bank), copied to the

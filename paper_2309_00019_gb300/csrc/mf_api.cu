@@ -46,6 +46,10 @@ struct mf_plan_s {
   unsigned* dmax = nullptr;       // per-detector max |q| (float bits)
   float* dscale = nullptr;        // per-detector power-of-two data scale
   int2* row_valid = nullptr;      // per-row analysed range (overlapping segments), or null
+  // chi^2 veto: band edges for chisq_p bands (valid until the bank or the PSD changes)
+  double* bpow = nullptr;
+  int32_t* edges = nullptr;
+  int chisq_p = 0;
   float2* scratch = nullptr;
   int batch = 1;
   unsigned long long* slots = nullptr;
@@ -188,6 +192,7 @@ void make_weights(const mf_plan_desc& d, const double* psd, std::vector<double>&
 
 mf_status recompute_sigmasq(mf_plan_t p, int64_t row0, int64_t n_rows) {
   p->scale_valid = false;
+  p->chisq_p = 0;  // band edges follow the bank and the PSD
   if (!p->psd_set || !p->bank || n_rows <= 0) return MF_OK;
   cudaError_t e = mf::launch_sigmasq(p->bank, bank_type(p->bank_dtype), p->ld_bank, p->scales_dev, row0, n_rows,
                                      p->w_dev, p->nb, p->sigmasq_dev, p->inv_sigma_dev, p->st, p->n1, p->n2);
@@ -316,7 +321,7 @@ void mf_destroy(mf_plan_t p) {
   dfree(p->w_dev); dfree(p->bank); dfree(p->scales_dev); dfree(p->sigmasq_dev); dfree(p->inv_sigma_dev); dfree(p->ratio_dev); dfree(p->thr_raw_dev);
   dfree(p->sel_all); dfree(p->q); dfree(p->scratch); dfree(p->slots); dfree(p->sel_copy); dfree(p->trig);
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
-  dfree(p->q_lp); dfree(p->dmax); dfree(p->dscale); dfree(p->row_valid);
+  dfree(p->q_lp); dfree(p->dmax); dfree(p->dscale); dfree(p->row_valid); dfree(p->bpow); dfree(p->edges);
   dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -341,6 +346,7 @@ mf_status mf_bank_reserve(mf_plan_t p, mf_dtype dtype, int64_t n_tmpl) {
   cudaStreamSynchronize(p->st);
   p->n_tmpl = 0;
   p->scale_valid = false;
+  p->chisq_p = 0;
   p->bank_dtype = dtype;
   p->ld_bank = p->d.n / 2;  // column layout of the N/2 bins below Nyquist (launch_to_cols)
   const size_t bytes = (size_t)n_tmpl * p->ld_bank * elem_bytes(dtype);
@@ -681,6 +687,62 @@ mf_status mf_get_triggers(mf_plan_t p, mf_trigger* out, int64_t cap, int64_t* n_
   }
   if (n > cap || n > p->d.max_triggers)
     return fail(p, MF_EOVERFLOW, "mf_get_triggers: " + std::to_string(n) + " triggers exceed the buffer");
+  return MF_OK;
+}
+
+mf_status mf_chisq(mf_plan_t p, int32_t n_bands, float* chi2, float* newsnr) {
+  if (!p || !chi2 || !newsnr) return fail(p, MF_EINVAL, "mf_chisq: null argument");
+  if (n_bands < 2 || n_bands > 64) return fail(p, MF_EINVAL, "mf_chisq: bands must be in [2, 64]");
+  if (!p->filtered) return fail(p, MF_ESTATE, "mf_chisq: no filter run");
+  if (p->chisq_p != n_bands) {
+    mf_status s;
+    if ((s = dalloc(p, &p->bpow, (size_t)p->n_tmpl * mf::chisq_blocks(p->n1, p->n2) * sizeof(double), "band power")) !=
+            MF_OK ||
+        (s = dalloc(p, &p->edges, (size_t)p->n_tmpl * (n_bands + 1) * sizeof(int32_t), "band edges")) != MF_OK)
+      return s;
+    cudaError_t e = mf::launch_chisq_edges(p->bank, bank_type(p->bank_dtype), p->ld_bank, p->n_tmpl, p->n1, p->n2,
+                                           p->w_dev, p->nb, p->bpow, n_bands, p->edges, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "mf_chisq band edges");
+    p->chisq_p = n_bands;
+  }
+  const bool lp = p->data_dtype != MF_F32;
+  cudaError_t e = mf::launch_chisq(p->trig, p->count, p->d.max_triggers, p->bank, bank_type(p->bank_dtype), p->ld_bank,
+                                   lp ? p->q_lp : (const void*)p->q, bank_type(p->data_dtype), p->ld_q, p->n1, p->n2,
+                                   p->edges, n_bands, p->ratio_dev, lp ? p->dscale : nullptr, chi2, newsnr, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_chisq");
+  return MF_OK;
+}
+
+mf_status mf_far(const float* stat_fg, int64_t n_fg, const float* stat_bg, int64_t n_bg, double t_bg, double scale,
+                 double fit_min, double* far_count, double* far_fit, double* alpha, double* beta) {
+  if (n_fg < 0 || n_bg < 0 || (n_fg > 0 && (!stat_fg || !far_count)) || (n_bg > 0 && !stat_bg))
+    return fail(nullptr, MF_EINVAL, "mf_far: null argument or negative size");
+  if (!(t_bg > 0) || !(scale > 0)) return fail(nullptr, MF_EINVAL, "mf_far: t_bg and scale must be positive");
+  std::vector<double> bg(stat_bg, stat_bg + n_bg);
+  std::sort(bg.begin(), bg.end());
+  auto count_ge = [&](double x) {
+    return scale * (double)(bg.end() - std::lower_bound(bg.begin(), bg.end(), x));
+  };
+  for (int64_t i = 0; i < n_fg; ++i) far_count[i] = (1.0 + count_ge((double)stat_fg[i])) / t_bg;
+  // least-squares line through (x, log n_b(x)) at every background value x >= fit_min
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  int64_t m = 0;
+  for (size_t i = std::lower_bound(bg.begin(), bg.end(), fit_min) - bg.begin(); i < bg.size(); ++i) {
+    const double x = bg[i], y = std::log(scale * (double)(bg.size() - (std::lower_bound(bg.begin(), bg.end(), x) - bg.begin())));
+    sx += x;
+    sy += y;
+    sxx += x * x;
+    sxy += x * y;
+    ++m;
+  }
+  const double det = (double)m * sxx - sx * sx;
+  const bool ok = m >= 2 && det > 0;
+  const double b = ok ? ((double)m * sxy - sx * sy) / det : std::nan("");
+  const double a = ok ? (sy - b * sx) / (double)m : std::nan("");
+  if (alpha) *alpha = a;
+  if (beta) *beta = b;
+  if (far_fit)
+    for (int64_t i = 0; i < n_fg; ++i) far_fit[i] = ok ? (1.0 + std::exp(a + b * (double)stat_fg[i])) / t_bg : std::nan("");
   return MF_OK;
 }
 

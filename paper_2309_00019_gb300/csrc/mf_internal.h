@@ -99,6 +99,16 @@ cudaError_t launch_prep_cols(const float2* dtilde, int64_t ld_d, const double* w
                              float2* q, int64_t ld_q, unsigned long long* slots, int64_t n_slots, cudaStream_t st,
                              double q_scale);
 
+// chi^2 veto at trigger times (mf_chisq.cu): band edges of every template for
+// p bands (bpow: n_tmpl x chisq_blocks scratch, edges: n_tmpl x (p + 1)), then
+// chi^2 and the re-weighted SNR of the first min(*count, cap) triggers.
+int64_t chisq_blocks(int n1, int n2);
+cudaError_t launch_chisq_edges(const void* bank, int bank_type, int64_t ld_bank, int64_t n_tmpl, int n1, int n2,
+                               const double* w, int64_t nb, double* bpow, int p, int32_t* edges, cudaStream_t st);
+cudaError_t launch_chisq(const void* trig, const int64_t* count, int64_t cap, const void* bank, int bank_type,
+                         int64_t ld_bank, const void* q, int q_type, int64_t ld_q, int n1, int n2, const int32_t* edges,
+                         int p, const float* ratio, const float* dscale, float* chi2, float* newsnr, cudaStream_t st);
+
 // One CTA of 128 threads waiting on a barrier nothing completes (bounded waits
 // record a timeout in *status; *returned counts the threads that returned).
 cudaError_t launch_wait_selftest(int* status, int* returned, cudaStream_t st);

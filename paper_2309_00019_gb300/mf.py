@@ -89,6 +89,8 @@ SIGNATURES = {
     "mf_set_data_dtype": (C.c_int, [_P, C.c_int]),
     "mf_set_row_valid": (C.c_int, [_P, _P]),
     "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "mf_chisq": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mf_far": (C.c_int, [_P, _I64, _P, _I64, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P]),
     "mf_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(mf_batch_desc)]),
     "mf_batch_destroy": (None, [_P]),
     "mf_batch_last_error": (C.c_char_p, [_P]),
@@ -245,6 +247,10 @@ class Plan:
         """Per-row analysed ranges, int64 [n_det, 2] (None restores the plan's range)."""
         r = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
         _check(self.h, self.lib.mf_set_row_valid(self.h, _ptr(r)))
+
+    def chisq(self, n_bands, chi2, newsnr):
+        """chi^2 and the re-weighted SNR of the last filter's triggers into device float arrays."""
+        _check(self.h, self.lib.mf_chisq(self.h, n_bands, _ptr(chi2), _ptr(newsnr)))
 
     def selftest_wait(self):
         """Run the bounded-wait self-test; returns the number of threads that came back."""
@@ -462,3 +468,18 @@ class Batch:
         st = self.lib.mf_batch_get_triggers(self.h, out.ctypes.data if n.value else None, n.value, C.byref(n))
         _bcheck(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
         return out, n.value, st
+
+
+def far(stat_fg, stat_bg, t_bg, scale=1.0, fit_min=None):
+    """mf_far: (far_count, far_fit, alpha, beta) for foreground / background statistics."""
+    lib = load()
+    fg = np.ascontiguousarray(stat_fg, dtype=np.float32)
+    bg = np.ascontiguousarray(stat_bg, dtype=np.float32)
+    fc = np.zeros(len(fg))
+    ff = np.zeros(len(fg))
+    a, b = C.c_double(), C.c_double()
+    fm = float(np.min(bg)) if fit_min is None and len(bg) else (0.0 if fit_min is None else fit_min)
+    _check(None, lib.mf_far(_ptr(fg) if len(fg) else None, len(fg), _ptr(bg) if len(bg) else None, len(bg),
+                            float(t_bg), float(scale), fm, _ptr(fc) if len(fg) else None,
+                            _ptr(ff) if len(fg) else None, C.byref(a), C.byref(b)))
+    return fc, ff, a.value, b.value

@@ -35,7 +35,7 @@ class PairSet:
 
 
 def generate_pairs(n_pairs, coarse_m1, coarse_m2, fine_m1, fine_m2, nbhd_ptr, nbhd_idx, seed=0, T=32.0,
-                   fs1=512.0, fs2=2048.0, f_low=30.0, snr_range=(8.0, 20.0), per_call=8, thr1=5.0, thr2=4.0,
+                   fs1=512.0, fs2=2048.0, f_low=30.0, snr_range=(8.0, 20.0), per_call=64, thr1=5.0, thr2=4.0,
                    max_slots=2000, device="cuda:0"):
     """Training pairs from injection runs filtered by libmf (see the module header)."""
     import torch

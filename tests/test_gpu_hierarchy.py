@@ -72,3 +72,34 @@ def test_end_to_end_from_host_strain(small_run):
     trig_dev, _, _ = h.p2.triggers()
     assert np.array_equal(trig2, trig_dev)
     assert len(co) > 0
+
+
+def test_background_far_of_the_coincidences(small_run):
+    """Eq. (6) and the Sec. IV tail fit through mf_far on the run's own
+    coincidences (zero lag = foreground, shifted = background) against the oracle."""
+    from paper_2309_00019_gb300 import mf
+
+    c, h = small_run["c"], small_run["h"]
+    co, _, _ = h.p1.coincs()
+    fg = co["rho_c"][co["shift"] == 0]
+    bg = co["rho_c"][co["shift"] > 0]
+    assert len(fg) > 0 and len(bg) > 2
+    t_bg = c.n_shifts * (c.n1 / c.fs1)
+    fit_min = float(np.sort(bg)[len(bg) // 3])
+    fc, ff, a, b = mf.far(fg, bg, t_bg, scale=3.0, fit_min=fit_min)
+    fg64, bg64 = fg.astype(np.float64), bg.astype(np.float64)
+    assert np.array_equal(fc, O.far_count(fg64, bg64, t_bg, scale=3.0))
+    ra, rb = O.tail_fit(bg64, fit_min, scale=3.0)
+    assert a == pytest.approx(ra, rel=1e-9, abs=1e-9) and b == pytest.approx(rb, rel=1e-9, abs=1e-9)
+    assert np.allclose(ff, O.far_fit(fg64, ra, rb, t_bg), rtol=1e-9)
+
+
+def test_far_edge_cases(lib):
+    from paper_2309_00019_gb300 import mf
+
+    fc, ff, a, b = mf.far([8.0, 9.0], [7.0], 10.0, fit_min=5.0)
+    assert np.allclose(fc, [0.1, 0.1]) and np.isnan(a) and np.all(np.isnan(ff))  # one value: no fit
+    fc, ff, a, b = mf.far([7.0], [7.0, 7.0, 8.0], 2.0, fit_min=7.0)
+    assert fc[0] == pytest.approx(2.0)  # (1 + 3) / 2: ties count
+    with pytest.raises(mf.MFError):
+        mf.far([1.0], [1.0], 0.0)

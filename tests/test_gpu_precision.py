@@ -131,7 +131,7 @@ def test_config4_full_bank_16bit_vs_fp32_and_oracle(mf):
         ti = np.array(synth.chirp_times(c.inj["m1"][i], c.inj["m2"][i], c.f_low))
         ids.append(int(np.argmin(((tau - ti) / tau.std(axis=0)) ** 2 @ np.ones(2))))
     ids = sorted(set(ids) | set(int(x) for x in rng.choice(nt, 6, replace=False)))
-    res = {}
+    res, ms = {}, {}
     for kind in ("f32", "f16", "bf16"):
         dt = {"f32": 0, "f16": 1, "bf16": 2}[kind]
         p = mf.Plan(c.fs, n, 2, c.f_low, c.fs / 2, c.thr, c.window, dtype=dt, max_triggers=1 << 24)
@@ -144,7 +144,14 @@ def test_config4_full_bank_16bit_vs_fp32_and_oracle(mf):
                 p.bank_quantize_rows(r0, rows, ld=ld, on_device=1)
         if dt:
             p.set_data_dtype(dt)
+        p.filter(d, ld=ld)  # warm-up (tables, scales)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         p.filter(d, ld=ld)
+        e1.record()
+        e1.synchronize()
+        ms[kind] = e0.elapsed_time(e1)
         trig, cnt, _ = p.triggers()
         assert cnt == len(trig)
         res[kind] = trig
@@ -161,7 +168,9 @@ def test_config4_full_bank_16bit_vs_fp32_and_oracle(mf):
         tr = res[kind]
         sub = tr[np.isin(tr["tmpl"], ids)]
         st = compare_triggers(sub, rho2, ids, c.thr, c.window, rel_tie=4 * tol, snr_rtol=tol)
-        line = (f"\nconfig 4 {kind}: {len(tr)} triggers; oracle sample ({len(ids)} templates, "
+        tds = nt * 2 * (n / c.fs) / (ms[kind] * 1e-3)
+        line = (f"\nconfig 4 {kind}: filter {ms[kind]:.1f} ms ({tds:.3g} template-s/s), {len(tr)} triggers; "
+                f"oracle sample ({len(ids)} templates, "
                 f"{st['exact'] + st['tie_swaps']} triggers): max rel SNR err {st['max_rel_snr']:.2e} (bound {tol:.1e})")
         if kind != "f32":
             k = _keys(tr, nt, c.window)
