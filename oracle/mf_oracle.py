@@ -168,6 +168,41 @@ def filter_bank(stilde, bank, psd, n, fs, f_low, f_high, thr, window,
 
 
 # ---------------------------------------------------------------------------
+# PSD estimation upstream of the filter (the paper takes S_n from the data)
+# ---------------------------------------------------------------------------
+
+def median_bias(n):
+    """Ratio of the median to the mean of n exponential periodogram values
+    (FINDCHIRP, Allen et al., Appendix B): 1 - 1/2 + 1/3 - ... up to 1/(2m+1),
+    m = (n - 1) // 2."""
+    m = (n - 1) // 2
+    return 1.0 + sum(1.0 / (2 * i + 1) - 1.0 / (2 * i) for i in range(1, m + 1))
+
+
+def psd_welch(strain, fs, seg_len, stride, average="median"):
+    """One-sided PSD of each row of strain by Welch's method: segments of
+    seg_len samples every stride samples (those that fit), periodic Hann
+    window w[j] = (1 - cos(2 pi j / seg_len)) / 2, no detrending,
+    P[k] = c |sum_j w[j] x[j] e^{-2 pi i j k / n}|^2 / (fs sum_j w[j]^2) with
+    c = 2 except at DC and Nyquist (c = 1); averaged over segments by the
+    mean, or by the median divided by median_bias (reading: the paper does
+    not describe its PSD estimate)."""
+    x = np.atleast_2d(np.asarray(strain, dtype=np.float64))
+    n_seg = (x.shape[1] - seg_len) // stride + 1
+    j = np.arange(seg_len)
+    w = 0.5 - 0.5 * np.cos(2 * math.pi * j / seg_len)
+    out = np.zeros((x.shape[0], seg_len // 2 + 1))
+    for d in range(x.shape[0]):
+        per = np.empty((n_seg, seg_len // 2 + 1))
+        for s in range(n_seg):
+            X = np.fft.rfft(x[d, s * stride:s * stride + seg_len] * w)
+            per[s] = np.abs(X) ** 2 / (fs * np.sum(w * w))
+        per[:, 1:-1] *= 2.0
+        out[d] = per.mean(axis=0) if average == "mean" else np.median(per, axis=0) / median_bias(n_seg)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # signal-based veto at trigger times: chi^2_r and the re-weighted SNR (Eq. 4)
 # ---------------------------------------------------------------------------
 
