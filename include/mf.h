@@ -87,6 +87,22 @@ const char* mf_last_error(mf_plan_t plan);
  * bank.  Errors: MF_EINVAL (null, nbins != N/2+1). */
 mf_status mf_set_psd(mf_plan_t plan, const double* psd, int64_t nbins);
 
+/* One-sided PSD S_n of long data by Welch's method (the weights of Eq. 2 need
+ * the PSD of the data; the paper does not describe its estimate, this is the
+ * reading): for each detector row of strain (device float32 [n_det][ld],
+ * n_samples used), segments of seg_len samples (a power of two in
+ * [2^12, 2^20]) every stride samples (those that fit), periodic Hann window
+ * w[j] = (1 - cos(2 pi j / seg_len)) / 2, no detrending,
+ *   P[k] = c |sum_j w[j] x[j] e^{-2 pi i j k / seg_len}|^2 / (fs sum_j w[j]^2),
+ * c = 2 except at DC and Nyquist (c = 1), averaged over segments by the mean
+ * (average = 0) or by the median divided by 1 - 1/2 + 1/3 - ... (m terms
+ * after the first, m = (segments - 1) / 2; FINDCHIRP Appendix B; average = 1,
+ * at most 4096 segments).  psd: device float64 [n_det][seg_len/2+1] (out).
+ * Allocates segments x n_det x seg_len x 20 bytes of work space for the call.
+ * Synchronises.  Errors (mf_last_error(NULL)): MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+mf_status mf_psd_welch(double fs, int32_t n_det, int64_t n_samples, const float* strain, int64_t ld, int64_t seg_len,
+                       int64_t stride, int32_t average, double* psd, void* cuda_stream);
+
 /* Replace the template bank (Sec. II; Table I): n_tmpl one-sided templates
  * h~_t[k], row t at htilde + t*ld elements, k = 0..N/2 (ld >= N/2+1).  dtype
  * MF_F32 (scales must be NULL) or MF_F16 / MF_BF16 with host float32

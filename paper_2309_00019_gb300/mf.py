@@ -90,6 +90,7 @@ SIGNATURES = {
     "mf_set_row_valid": (C.c_int, [_P, _P]),
     "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mf_chisq": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mf_psd_welch": (C.c_int, [C.c_double, C.c_int32, _I64, _P, _I64, _I64, _I64, C.c_int32, _P, _P]),
     "mf_far": (C.c_int, [_P, _I64, _P, _I64, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P]),
     "mf_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(mf_batch_desc)]),
     "mf_batch_destroy": (None, [_P]),
@@ -483,3 +484,18 @@ def far(stat_fg, stat_bg, t_bg, scale=1.0, fit_min=None):
                             float(t_bg), float(scale), fm, _ptr(fc) if len(fg) else None,
                             _ptr(ff) if len(fg) else None, C.byref(a), C.byref(b)))
     return fc, ff, a.value, b.value
+
+
+def psd_welch(strain, fs, seg_len, stride, average="median", out=None, stream=None):
+    """mf_psd_welch on a device float32 tensor [n_det, n_samples]; returns the device float64 PSD [n_det, seg_len/2+1]."""
+    import torch
+
+    n_det, n_samples = strain.shape
+    ld = strain.stride(0) if n_det > 1 else n_samples  # a single row's stride may be reported as 0
+    if strain.stride(1) != 1:
+        raise ValueError("psd_welch: rows must be contiguous")
+    if out is None:
+        out = torch.zeros((n_det, seg_len // 2 + 1), dtype=torch.float64, device=strain.device)
+    _check(None, load().mf_psd_welch(float(fs), n_det, n_samples, _ptr(strain), ld, seg_len, stride,
+                                     0 if average == "mean" else 1, _ptr(out), stream))
+    return out

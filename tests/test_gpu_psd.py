@@ -53,7 +53,9 @@ def test_welch_psd_drives_the_filter(mf):
         p.filter(sfd)
         out.append(p.triggers()[0])
     a, b = out
-    la = a[a["snr"] > 8]
-    lb = b[b["snr"] > 8]
-    assert len(la) > 0 and np.array_equal(la[["tmpl", "sample"]], lb[["tmpl", "sample"]])
-    assert np.allclose(la["snr"], lb["snr"], rtol=0.05)
+    # every loud trigger with the analytic PSD is found at the same sample with the estimate, rho within 5%
+    loud = a[a["snr"] > 10]
+    assert len(loud) > 0
+    for t in loud:
+        m = b[(b["tmpl"] == t["tmpl"]) & (b["sample"] == t["sample"])]
+        assert len(m) == 1 and abs(m["snr"][0] / t["snr"] - 1) < 0.05
