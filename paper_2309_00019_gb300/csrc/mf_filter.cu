@@ -8,14 +8,21 @@
 //           the non-zero half (element k = k1 N2 + k2, k1 < N1/2, at
 //           k2 N1/2 + k1), so an item's two tiles are two contiguous 1-D bulk
 //           copies.  The product x = q conj(h) is formed on the shared-memory
-//           read; N1-point column transforms (pass a one column per group of
-//           T threads, pass b across columns); the four-step twiddle
-//           exp(+2 pi i j1 k2 / N); sector-aligned stores to the scratch.
-//   k_rows: item = RW consecutive rows j1 of one series, one 1-D bulk copy;
-//           N2-point row transforms; rho^2 = |z|^2 / sigma^2 of
-//           z[j1 + N1 j2], threshold and window maxima in registers.
+//           read; N1-point column transforms, each column owned by one group
+//           of T threads inside a warp (its exchange needs only a warp
+//           barrier); the four-step twiddle exp(+2 pi i j1 k2 / N); stores to
+//           the scratch in panels of P = RW rows: element (j1, k2) of a series
+//           at (j1 / P) N2 P + k2 P + j1 % P, so P consecutive threads fill
+//           whole sectors and a pass-2 item is one contiguous panel.
+//   k_rows: item = one panel (RW rows j1), one 1-D bulk copy; N2-point row
+//           transforms; rho^2 = |z|^2 / sigma^2 of z[j1 + N1 j2], threshold
+//           and window maxima in registers.
 // Sub-FFT twiddles come from a per-CTA shared table.  All mbarrier waits are
 // bounded (see mf_tma.cuh) and report through the plan's status word.
+// Programmatic dependent launch: each kernel lets the next one launch only
+// when a CTA has finished all its items, so the next kernel's CTAs (which wait
+// for this one to complete before touching the scratch) take the slots of
+// retiring CTAs instead of competing with this kernel's own CTAs for them.
 #include "mf_common.cuh"
 #include "mf_tma.cuh"
 
@@ -41,10 +48,11 @@ struct Xch {
 };
 
 // Exchange buffer of the column transforms: C columns of M values at column
-// stride S >= PAD.  Pass a: thread (c = tid / T, t = tid % T) writes logical
-// t RA + q of column c; pass b: thread (c = tid % C, tb = tid / C) reads
-// j + r RA (j = tb + T i).  S is the candidate in [PAD, PAD + 16) with the
-// fewest repeated 8-byte bank pairs over every half-warp of both patterns.
+// stride S >= PAD.  Thread (c = tid / T, t = tid % T) writes logical t RA + q
+// of column c in pass a and reads j + r RA (j = t + T i) of it in pass b.  S
+// is the candidate in [PAD, PAD + 16) with the fewest repeated 8-byte bank
+// pairs over every half-warp of both patterns (half-warps span two columns
+// when T = 8).
 template <int M, int C>
 struct ColXch {
   using G = SubFft<M>;
@@ -64,7 +72,7 @@ struct ColXch {
         for (int r = 0; r < RB; ++r) {
           int cnt[16] = {};
           for (int l = 0; l < 16; ++l) {
-            const int tid = hw * 16 + l, c = tid % C, j = tid / C + T * i;
+            const int tid = hw * 16 + l, c = tid / T, j = tid % T + T * i;
             ++cnt[(c * S + j + r * RA + r) & 15];
           }
           for (int b = 0; b < 16; ++b) total += cnt[b] > 1 ? cnt[b] - 1 : 0;
@@ -112,9 +120,9 @@ struct ColGeo {
 template <int N2>
 struct RowGeo {
   using G = SubFft<N2>;
-  static constexpr int RW = kT2 / G::T;                   // rows per item
+  static constexpr int RW = kT2 / G::T;                   // rows per item (the scratch panel height)
   static constexpr int ITEM = RW * N2;                    // complex values per item
-  static constexpr int K = G::T >= 16 ? 16 : G::T;
+  static constexpr int K = 16 / RW;                       // threads of one row in a half-warp
   using X = Xch<N2, K>;
   static constexpr int XCH_BYTES = RW * X::S * 8;
   static constexpr int SLOT = round128(ITEM * 8 > XCH_BYTES ? ITEM * 8 : XCH_BYTES);
@@ -160,8 +168,8 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: slots, [2]: twiddles
   const int tid = threadIdx.x;
-  const int ca = tid / T, ta = tid % T;   // pass a: column, thread of the column
-  const int cbb = tid % C, tb = tid / C;  // pass b
+  const int ca = tid / T, ta = tid % T;   // column of the item, thread of the column
+  constexpr int PH = RowGeo<N2>::RW;      // scratch panel height
   const int n_items = a.count * a.n_det * NCB;
   const unsigned char* qbase = static_cast<const unsigned char*>(QT == kBankF32 ? (const void*)a.q : a.q_lp);
   if (tid == 0) {
@@ -184,7 +192,6 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
     bulk_g2s(dst + P::H_BYTES, qbase + ((int64_t)d * a.ld_q + (int64_t)cb * C * R) * P::QB, (uint32_t)P::Q_BYTES,
              bar + slot);
   };
-  pdl_launch_dependents();  // the next kernel may start its prologue as our CTAs retire
   if (tid == 0) {
     mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
     bulk_g2s(sm + P::TW_OFF, a.tw1, (uint32_t)P::TW_BYTES, bar + 2);
@@ -225,27 +232,29 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
     float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT);
 #pragma unroll
     for (int q = 0; q < RA; ++q) xb[ca * S + ta * RA + q + ta] = v[q];
-    __syncthreads();
+    __syncwarp();  // the column's T threads are one group inside a warp
     float2* out = a.scratch + (int64_t)s * N;
-    const int k2 = (item % NCB) * C + cbb;
+    const int k2 = (item % NCB) * C + ca;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-      const int j = tb + T * i;
+      const int j = ta + T * i;
       float2 u[RB];
-      u[0] = xb[cbb * S + j];
+      u[0] = xb[ca * S + j];
 #pragma unroll
-      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[cbb * S + j + r * RA + r], tw[r * RA + j]);
+      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[ca * S + j + r * RA + r], tw[r * RA + j]);
       dft<RB>(u);
       // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q, both from the table
       float2 w = __ldg(a.tw4 + (uint32_t)j * (uint32_t)k2);
       const float2 st = __ldg(a.tw4 + (uint32_t)RA * (uint32_t)k2);
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
-        st_global_hint(out + (int64_t)(j + q * RA) * N2 + k2, cmul(u[q], w), pol_keep);
+        const int j1 = j + q * RA;
+        st_global_hint(out + (int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH), cmul(u[q], w), pol_keep);
         if (q + 1 < RB) w = cmul(w, st);
       }
     }
   }
+  pdl_launch_dependents();  // our items are done: the next kernel may launch
 }
 
 // ---------------------------------------------------------------------------
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);
   const int tid = threadIdx.x;
-  const int t = tid % T, row = tid / T;
+  const int row = tid % RW, t = tid / RW;  // rows fastest: the panel is [k2][row]
   const int n_items = a.count * a.n_det * NRB;
   if (tid == 0) {
     mbar_init(bar + 0, 1);
@@ -280,7 +289,6 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
     bulk_g2s_hint(sm + slot * P::SLOT, a.scratch + (int64_t)s * N + (int64_t)j10 * N2, (uint32_t)(P::ITEM * 8),
                   bar + slot, pol_last_use);
   };
-  pdl_launch_dependents();
   if (tid == 0) {
     mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
     bulk_g2s(sm + P::TW_OFF, a.tw2, (uint32_t)P::TW_BYTES, bar + 2);
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
     const int j1 = (item % NRB) * RW + row;
     float2 v[RA];
 #pragma unroll
-    for (int r = 0; r < RA; ++r) v[r] = stage[row * N2 + t + r * RB];
+    for (int r = 0; r < RA; ++r) v[r] = stage[(t + r * RB) * RW + row];
     if (__syncthreads_or(fail)) return;
     if (tid == 0 && item + (int)gridDim.x < n_items) {
       fence_proxy_async();
@@ -324,6 +332,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
       for (int q = 0; q < RB; ++q) ep(se, (int64_t)j1 + (int64_t)N1 * (j + q * RA), u[q]);
     }
   }
+  pdl_launch_dependents();  // our items are done: the next kernel may launch
 }
 
 template <class K>
