@@ -80,7 +80,7 @@ struct mf_plan_s {
   // TMA-staged filter
   int* status = nullptr;    // device status word
   float2* tw = nullptr;     // sub-FFT twiddle tables [2][1024]
-  float2* tw4 = nullptr;    // four-step twiddles w_N^m, m < 32 * N2
+  float2* tw4 = nullptr;    // four-step twiddles by column (launch_fill_tw4)
   // instrumentation
   mf_plan_stats stats{};
   bool prof = false;
@@ -298,7 +298,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
       (s = dalloc(p, &p->count, sizeof(int64_t), "count")) != MF_OK ||
       (s = dalloc(p, &p->status, sizeof(int), "status")) != MF_OK ||
       (s = dalloc(p, &p->tw, 2 * 1024 * sizeof(float2), "twiddles")) != MF_OK ||
-      (s = dalloc(p, &p->tw4, (size_t)32 * p->n2 * sizeof(float2), "four-step twiddles")) != MF_OK) {
+      (s = dalloc(p, &p->tw4, (size_t)mf::tw4_count(d.n) * sizeof(float2), "four-step twiddles")) != MF_OK) {
     g_err = p->err;
     mf_destroy(p);
     return s;
@@ -306,7 +306,7 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   cudaMemsetAsync(p->count, 0, sizeof(int64_t), p->st);
   cudaMemsetAsync(p->status, 0, sizeof(int), p->st);
   if (mf::launch_fill_twiddles(d.n, p->tw, p->tw + 1024, p->st) != cudaSuccess ||
-      mf::launch_fill_tw4(d.n, p->tw4, (int64_t)32 * p->n2, p->st) != cudaSuccess) {
+      mf::launch_fill_tw4(d.n, p->tw4, p->st) != cudaSuccess) {
     g_err = "mf_plan: twiddle table kernel";
     mf_destroy(p);
     return MF_ECUDA;

@@ -243,14 +243,25 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
 #pragma unroll
       for (int r = 1; r < RB; ++r) u[r] = cmul(xb[ca * S + j + r * RA + r], tw[r * RA + j]);
       dft<RB>(u);
-      // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q, both from the table
-      float2 w = __ldg(a.tw4 + (uint32_t)j * (uint32_t)k2);
-      const float2 st = __ldg(a.tw4 + (uint32_t)RA * (uint32_t)k2);
+      // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q; the table row of
+      // column k2 holds w_N^{j k2} for j <= RA, so a warp's loads are contiguous
+      const float2* twr = a.tw4 + (int64_t)k2 * (RA + 1);
+      float2 w = __ldg(twr + j);
+      const float2 st = __ldg(twr + RA);
+      if constexpr (RA % PH == 0) {  // j + q RA stays in j's panel row: one base, constant panel steps
+        float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
 #pragma unroll
-      for (int q = 0; q < RB; ++q) {
-        const int j1 = j + q * RA;
-        st_global_hint(out + (int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH), cmul(u[q], w), pol_keep);
-        if (q + 1 < RB) w = cmul(w, st);
+        for (int q = 0; q < RB; ++q) {
+          st_global_hint(ob + (int64_t)q * (RA / PH) * (N2 * PH), cmul(u[q], w), pol_keep);
+          if (q + 1 < RB) w = cmul(w, st);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const int j1 = j + q * RA;
+          st_global_hint(out + (int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH), cmul(u[q], w), pol_keep);
+          if (q + 1 < RB) w = cmul(w, st);
+        }
       }
     }
   }
@@ -446,9 +457,26 @@ cudaError_t run_fill_tw(float2* tw1, float2* tw2, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__global__ void k_fill_tw4(float2* tw4, int64_t count, uint32_t n) {
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < count; m += (int64_t)gridDim.x * blockDim.x)
-    tw4[m] = unit_root((uint32_t)m, n);
+// four-step twiddles by column: tw4[k2 (ra + 1) + j] = w_N^{j k2}, j <= ra, k2 < n2
+__global__ void k_fill_tw4(float2* tw4, int n2, int ra, uint32_t n) {
+  const int64_t count = (int64_t)n2 * (ra + 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k2 = (uint32_t)(i / (ra + 1)), j = (uint32_t)(i % (ra + 1));
+    tw4[i] = unit_root((j * k2) % n, n);
+  }
+}
+
+template <int N1, int N2>
+cudaError_t run_fill_tw4(float2* tw4, cudaStream_t st) {
+  k_fill_tw4<<<64, 256, 0, st>>>(tw4, N2, SubFft<N1>::RA, (uint32_t)N1 * (uint32_t)N2);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+template <int N1, int N2>
+cudaError_t tw4_count_of(int64_t* c) {
+  *c = (int64_t)N2 * (SubFft<N1>::RA + 1);
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -457,10 +485,12 @@ cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISP
 
 cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH2(a.n, run_rows, (a, st)) }
 
-cudaError_t launch_fill_tw4(int64_t n, float2* tw4, int64_t count, cudaStream_t st) {
-  k_fill_tw4<<<64, 256, 0, st>>>(tw4, count, (uint32_t)n);
-  add_launches(1);
-  return cudaGetLastError();
+cudaError_t launch_fill_tw4(int64_t n, float2* tw4, cudaStream_t st) { MF_DISPATCH2(n, run_fill_tw4, (tw4, st)) }
+
+int64_t tw4_count(int64_t n) {
+  int64_t c = 0;
+  auto f = [&]() -> cudaError_t { MF_DISPATCH2(n, tw4_count_of, (&c)) };
+  return f() == cudaSuccess ? c : 0;
 }
 
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st) {

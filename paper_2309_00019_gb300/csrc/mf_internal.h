@@ -51,7 +51,7 @@ struct FilterArgs {
   const float2* tw1;        // sub-FFT twiddle tables (w_N1^{r j}, w_N2^{r j}), 8 KB max each
   const float2* tw2;
   const float* thr_raw;     // per template: rho_thr^2 / ratio^2 on the pre-scaled data (TMA kernels)
-  const float2* tw4;        // four-step twiddles w_N^m, m < RA(N1) * N2 (TMA kernels)
+  const float2* tw4;        // four-step twiddles by column (launch_fill_tw4)
   int first_batch;          // 1: the weighted data were written by the kernel just before (PDL ordering)
   // 16-bit weighted data (TMA kernels): q_lp [n_det][ld_q] half2 / bfloat162 holding c_d q, with
   // c_d = dscale[d] a power of two; q_type = kBankF32 means the FP32 q above is used
@@ -86,8 +86,10 @@ bool plan_capturable(const ::mf_plan_s* p);
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st);
-// w_N^m for m < count (count <= 32768)
-cudaError_t launch_fill_tw4(int64_t n, float2* tw4, int64_t count, cudaStream_t st);
+// four-step twiddles of k_cols by column: tw4[k2 (RA + 1) + j] = w_N^{j k2}, j <= RA(N1), k2 < N2;
+// tw4_count(n) entries
+cudaError_t launch_fill_tw4(int64_t n, float2* tw4, cudaStream_t st);
+int64_t tw4_count(int64_t n);
 
 // Column layout of spectra rows: dst[r][k2 N1/2 + k1] = src[r][k1 N2 + k2] for
 // k1 < N1/2, k2 < N2 (the bins k < N/2), elem_bytes 8 (complex64) or 4 (16-bit
