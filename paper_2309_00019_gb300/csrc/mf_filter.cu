@@ -47,14 +47,16 @@ struct Xch {
   __device__ __forceinline__ static int idx(int c, int i) { return c * S + G::pidx(i); }
 };
 
-// Exchange buffer of the column transforms: C columns of M values at column
-// stride S >= PAD.  Thread (c = tid / T, t = tid % T) writes logical t RA + q
-// of column c in pass a and reads j + r RA (j = t + T i) of it in pass b.  S
-// is the candidate in [PAD, PAD + 16) with the fewest repeated 8-byte bank
-// pairs over every half-warp of both patterns (half-warps span two columns
-// when T = 8).
-template <int M, int C>
-struct ColXch {
+// Column regions of k_cols: column c of an item owns S float2 of a slot,
+// first its template tile then its weighted-data tile (N1/2 values each) and,
+// once its threads hold those in registers, its exchange buffer.  Thread
+// (c = tid / T, t = tid % T) writes logical t RA + q of column c in pass a
+// and reads j + r RA (j = t + T i) in pass b.  S is the even candidate in
+// [base, base + 32), base = max(tiles, PAD), with the fewest repeated 8-byte
+// bank pairs over every half-warp of both patterns (half-warps span two
+// columns when T = 8); even keeps every region 16-byte aligned for TMA.
+template <int M, int C, int BASE>
+struct ColStride {
   using G = SubFft<M>;
   static constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB;
   static constexpr int conflicts(int S) {
@@ -81,8 +83,9 @@ struct ColXch {
     return total;
   }
   static constexpr int pick() {
-    int best = G::PAD, bc = conflicts(G::PAD);
-    for (int s = G::PAD + 1; s < G::PAD + 16; ++s) {
+    const int b0 = (BASE + 1) / 2 * 2;
+    int best = b0, bc = conflicts(b0);
+    for (int s = b0 + 2; s < b0 + 32; s += 2) {
       const int c = conflicts(s);
       if (c < bc) {
         bc = c;
@@ -94,27 +97,28 @@ struct ColXch {
   static constexpr int S = pick();
 };
 
-// Shared-memory plan of k_cols: two slots, each first the landing zone of an
-// item's two tiles (template, then weighted data, each [C][N1/2]) and then,
-// once those are in registers, the exchange buffer of the same item; the next
-// item's tiles land in the other slot.  Then the sub-FFT twiddles and barriers.
+constexpr int kColConsumers = kT2;             // compute threads of k_cols (4 warps)
+constexpr int kColThreads = kColConsumers + 32;  // plus one producer warp
+
+// Shared-memory plan of k_cols: two slots of C column regions (ColStride),
+// then the sub-FFT twiddles and the barriers full[2], empty[2], twiddles.
 template <int N1, int BT, int QT>
 struct ColGeo {
   using G = SubFft<N1>;
   static constexpr int T = G::T;                          // threads per column
-  static constexpr int C = kT2 / T;                       // columns per item
+  static constexpr int C = kColConsumers / T;             // columns per item
   static constexpr int R = N1 / 2;                        // non-zero half of k1
   static constexpr int HB = BT == kBankF32 ? 8 : 4;       // bytes per template element
   static constexpr int QB = QT == kBankF32 ? 8 : 4;       // bytes per weighted-data element
-  static constexpr int H_BYTES = C * R * HB;
-  static constexpr int Q_BYTES = C * R * QB;
-  using X = ColXch<N1, C>;
-  static constexpr int XCH_BYTES = C * X::S * 8;
-  static constexpr int SLOT = round128(H_BYTES + Q_BYTES > XCH_BYTES ? H_BYTES + Q_BYTES : XCH_BYTES);
+  static constexpr int H_COL = R * HB;                    // one column's template tile, bytes
+  static constexpr int Q_COL = R * QB;
+  static constexpr int TILES = (H_COL + Q_COL) / 8;
+  static constexpr int S = ColStride<N1, C, (TILES > G::PAD ? TILES : G::PAD)>::S;
+  static constexpr int SLOT = C * S * 8;
   static constexpr int TW_BYTES = G::RB * G::RA * 8;
   static constexpr int TW_OFF = 2 * SLOT;
   static constexpr int BAR_OFF = TW_OFF + round128(TW_BYTES);
-  static constexpr int SMEM = BAR_OFF + 32;
+  static constexpr int SMEM = BAR_OFF + 64;
 };
 
 template <int N2>
@@ -158,59 +162,79 @@ __global__ void k_fill_twiddles(float2* tw) {
 // ---------------------------------------------------------------------------
 
 template <int N1, int N2, int BT, int QT>
-__global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
+__global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   using G = SubFft<N1>;
   using P = ColGeo<N1, BT, QT>;
-  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::X::S;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
   constexpr int NCB = N2 / C;
   constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
+  constexpr int PH = RowGeo<N2>::RW;  // scratch panel height
   extern __shared__ __align__(128) unsigned char sm[];
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: slots, [2]: twiddles
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: tiles of the slot landed
+  uint64_t* empty = full + 2;                                     // [0], [1]: every warp done with the slot
+  uint64_t* twb = full + 4;                                       // the twiddle table landed
   const int tid = threadIdx.x;
-  const int ca = tid / T, ta = tid % T;   // column of the item, thread of the column
-  constexpr int PH = RowGeo<N2>::RW;      // scratch panel height
   const int n_items = a.count * a.n_det * NCB;
-  const unsigned char* qbase = static_cast<const unsigned char*>(QT == kBankF32 ? (const void*)a.q : a.q_lp);
   if (tid == 0) {
-    mbar_init(bar + 0, 1);
-    mbar_init(bar + 1, 1);
-    mbar_init(bar + 2, 1);
+    mbar_init(full + 0, 1);
+    mbar_init(full + 1, 1);
+    mbar_init(empty + 0, kColConsumers / 32);
+    mbar_init(empty + 1, kColConsumers / 32);
+    mbar_init(twb, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const uint64_t pol_stream = policy_evict_first();
-  const uint64_t pol_keep = policy_evict_last();
-  auto issue = [&](int item, int slot) {
-    const int s = item / NCB, cb = item % NCB;
-    const int b = s / a.n_det, d = s % a.n_det;
-    const int64_t tmpl = a.sel[a.pos0 + b];
-    unsigned char* dst = sm + slot * P::SLOT;
-    mbar_expect_tx(bar + slot, (uint32_t)(P::H_BYTES + P::Q_BYTES));
-    bulk_g2s_hint(dst, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + (int64_t)cb * C * R) * P::HB,
-                  (uint32_t)P::H_BYTES, bar + slot, pol_stream);
-    bulk_g2s(dst + P::H_BYTES, qbase + ((int64_t)d * a.ld_q + (int64_t)cb * C * R) * P::QB, (uint32_t)P::Q_BYTES,
-             bar + slot);
-  };
-  if (tid == 0) {
-    mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
-    bulk_g2s(sm + P::TW_OFF, a.tw1, (uint32_t)P::TW_BYTES, bar + 2);
-    // the weighted data come from the kernel just before only for the first batch; otherwise
-    // the first tiles (bank and data, both unchanged) load while the previous kernel drains
-    if (a.first_batch) {
-      pdl_wait();
-      fence_proxy_async_global_fwd();
+  if (tid >= kColConsumers) {
+    // producer warp: one lane issues every item's tiles into the slot its consumers released
+    if (tid == kColConsumers) {
+      const unsigned char* qbase = static_cast<const unsigned char*>(QT == kBankF32 ? (const void*)a.q : a.q_lp);
+      const uint64_t pol_stream = policy_evict_first();
+      mbar_expect_tx(twb, (uint32_t)P::TW_BYTES);
+      bulk_g2s(sm + P::TW_OFF, a.tw1, (uint32_t)P::TW_BYTES, twb);
+      // the weighted data come from the kernel just before only for the first batch; otherwise
+      // the first tiles (bank and data, both unchanged) load while the previous kernel drains
+      if (a.first_batch) {
+        pdl_wait();
+        fence_proxy_async_global_fwd();
+      }
+      int k = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+        const int slot = k & 1;
+        if (k >= 2 && !(ok = mbar_wait_bounded(empty + slot, (uint32_t)(((k >> 1) + 1) & 1), a.status))) break;
+        fence_proxy_async();
+        const int s = item / NCB, cb = item % NCB;
+        const int b = s / a.n_det, d = s % a.n_det;
+        const int64_t tmpl = a.sel[a.pos0 + b];
+        unsigned char* dst = sm + slot * P::SLOT;
+        mbar_expect_tx(full + slot, (uint32_t)(C * (P::H_COL + P::Q_COL)));
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int64_t col = (int64_t)cb * C + c;
+          bulk_g2s_hint(dst + c * S * 8, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + col * R) * P::HB,
+                        (uint32_t)P::H_COL, full + slot, pol_stream);
+          bulk_g2s(dst + c * S * 8 + P::H_COL, qbase + ((int64_t)d * a.ld_q + col * R) * P::QB, (uint32_t)P::Q_COL,
+                   full + slot);
+        }
+      }
+      // the consumers' last items are done: then let the next kernel launch
+      for (int m = k - 2; ok && m < k; ++m)
+        if (m >= 0) ok = mbar_wait_bounded(empty + (m & 1), (uint32_t)((m >> 1) & 1), a.status);
+      pdl_launch_dependents();
     }
-    if ((int)blockIdx.x < n_items) issue(blockIdx.x, 0);
+    return;
   }
+  // consumer warps: column ca of every item, T threads per column
+  const int ca = tid / T, ta = tid % T;
+  const uint64_t pol_keep = policy_evict_last();
   pdl_wait();  // the previous kernel (reader of the scratch we are about to write) has completed
-  if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) return;
+  if (!mbar_wait_bounded(twb, 0, a.status)) return;
   int k = 0;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
-    // every thread waits (bounded) for this item's tiles, reads its inputs, then one barrier
-    const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
-    const unsigned char* sh = sm + slot * P::SLOT;
+    if (!mbar_wait_bounded(full + slot, (uint32_t)((k >> 1) & 1), a.status)) break;
+    const unsigned char* col = sm + slot * P::SLOT + ca * S * 8;
     const int s = item / NCB;
     float2 v[RA];
 #pragma unroll
@@ -218,30 +242,25 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
       if (r >= RA / 2) {
         v[r] = make_float2(0.f, 0.f);
       } else {
-        const int idx = ca * R + ta + r * RB;  // k1 = ta + r RB < N1/2
-        v[r] = cmulc(smem_h<QT>(sh + P::H_BYTES, idx), smem_h<BT>(sh, idx));
+        const int idx = ta + r * RB;  // k1 < N1/2
+        v[r] = cmulc(smem_h<QT>(col + P::H_COL, idx), smem_h<BT>(col, idx));
       }
     }
-    // tiles consumed by every thread; the previous item (other slot) is finished too
-    if (__syncthreads_or(fail)) return;
-    if (tid == 0 && item + (int)gridDim.x < n_items) {
-      fence_proxy_async();
-      issue(item + gridDim.x, slot ^ 1);
-    }
+    __syncwarp();  // the column's tiles are read: its region becomes the exchange buffer
     dft<RA, true>(v);
-    float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT);
+    float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT) + ca * S;
 #pragma unroll
-    for (int q = 0; q < RA; ++q) xb[ca * S + ta * RA + q + ta] = v[q];
-    __syncwarp();  // the column's T threads are one group inside a warp
+    for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
+    __syncwarp();
     float2* out = a.scratch + (int64_t)s * N;
     const int k2 = (item % NCB) * C + ca;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = ta + T * i;
       float2 u[RB];
-      u[0] = xb[ca * S + j];
+      u[0] = xb[j];
 #pragma unroll
-      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[ca * S + j + r * RA + r], tw[r * RA + j]);
+      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[j + r * RA + r], tw[r * RA + j]);
       dft<RB>(u);
       // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q; the table row of
       // column k2 holds w_N^{j k2} for j <= RA, so a warp's loads are contiguous
@@ -264,6 +283,10 @@ __global__ void __launch_bounds__(kT2, 3) k_cols(FilterArgs a) {
         }
       }
     }
+    // this warp is done with the slot: order its shared accesses before the next bulk copy into it
+    fence_proxy_async();
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(empty + slot);
   }
   pdl_launch_dependents();  // our items are done: the next kernel may launch
 }
@@ -364,10 +387,10 @@ int sm_count() {
 
 // launch with programmatic stream serialization (overlaps our prologue with the previous kernel's tail)
 template <class K, class... Args>
-cudaError_t launch_pdl(K kern, int grid, int smem, cudaStream_t st, Args... args) {
+cudaError_t launch_pdl(K kern, int grid, int block, int smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kT2);
+  cfg.blockDim = dim3((unsigned)block);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -395,7 +418,7 @@ cudaError_t run_cols(const FilterArgs& a, cudaStream_t st) {
     attr = true;
   }
   const int items = a.count * a.n_det * (N2 / P::C);
-  cudaError_t e = launch_pdl(k, grid2(items), P::SMEM, st, a);
+  cudaError_t e = launch_pdl(k, grid2(items), kColThreads, P::SMEM, st, a);
   add_launches(1);
   return e;
 }
@@ -430,7 +453,7 @@ cudaError_t run_rows(const FilterArgs& a, cudaStream_t st) {
     attr = true;
   }
   const int items = a.count * a.n_det * (N1 / P::RW);
-  cudaError_t e = launch_pdl(k, grid2(items), P::SMEM, st, a);
+  cudaError_t e = launch_pdl(k, grid2(items), kT2, P::SMEM, st, a);
   add_launches(1);
   return e;
 }
