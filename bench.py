@@ -338,6 +338,10 @@ def main():
     roof = None
     hbm_gbs, hbm_kind = peaks()
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    try:  # measured FP32 FMA throughput (context for the derived peak)
+        alu_probe = mf.fma_probe()
+    except Exception:
+        alu_probe = None
     klist = []
     for d in kinds:
         per_ms = d["ms"] / d["launches"]
@@ -356,6 +360,8 @@ def main():
                 "flops_per_series": dom["flops_series"],
                 "flop_convention": "5 N log2(M) per series for an N-point transform built from M-point sub-FFTs",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+                "alu_probe_tflops": alu_probe,
+                "frac_of_probe": achieved / alu_probe if alu_probe else None,
                 "kernels": klist}
     # whole-step HBM view: template bytes the step must stream / step time
     step_bytes = (len(cfg.coarse_m1) * (hp.n1 // 2 + 1) + statistics.mean(unions) * (hp.n2 // 2 + 1)) * 8

@@ -250,6 +250,12 @@ mf_status mf_chisq(mf_plan_t plan, int32_t n_bands, float* chi2, float* newsnr);
  * Errors: MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
 mf_status mf_selftest_wait(mf_plan_t plan, int32_t* returned);
 
+/* Measured FP32 FMA throughput of the current device, TFLOP/s (2 flop per
+ * FMA; 8 independent chains per thread, 8 CTAs of 256 threads per SM, timed
+ * with CUDA events after a warm-up): context for the ALU roofline of the
+ * filter kernels.  Synchronises.  Errors: MF_EINVAL, MF_ECUDA. */
+mf_status mf_fma_probe(double* tflops, void* cuda_stream);
+
 /* ---- two-detector coincidence and follow-up (Sec. III) ---------------- */
 
 typedef struct {

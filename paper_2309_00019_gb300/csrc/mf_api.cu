@@ -746,6 +746,34 @@ mf_status mf_far(const float* stat_fg, int64_t n_fg, const float* stat_bg, int64
   return MF_OK;
 }
 
+mf_status mf_fma_probe(double* tflops, void* cuda_stream) {
+  if (!tflops) return fail(nullptr, MF_EINVAL, "mf_fma_probe: null argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::max(1, sms) * 8, iters = 4096;
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, (size_t)blocks * 256 * sizeof(float));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = mf::launch_fma_probe(out, blocks, iters / 8, st);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = mf::launch_fma_probe(out, blocks, iters, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(nullptr, MF_ECUDA, std::string("mf_fma_probe: ") + cudaGetErrorString(e));
+  const double flops = 2.0 * (double)blocks * 256.0 * 8.0 * 16.0 * (double)iters;
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return MF_OK;
+}
+
 mf_status mf_selftest_wait(mf_plan_t p, int32_t* returned) {
   if (!p || !returned) return fail(p, MF_EINVAL, "mf_selftest_wait: null argument");
   int* cnt = nullptr;

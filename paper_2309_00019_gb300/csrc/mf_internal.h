@@ -111,6 +111,9 @@ cudaError_t launch_chisq(const void* trig, const int64_t* count, int64_t cap, co
                          int64_t ld_bank, const void* q, int q_type, int64_t ld_q, int n1, int n2, const int32_t* edges,
                          int p, const float* ratio, const float* dscale, float* chi2, float* newsnr, cudaStream_t st);
 
+// blocks x 256 threads, each 8 chains x 16 x iters FP32 FMAs (the ALU probe)
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t st);
+
 // One CTA of 128 threads waiting on a barrier nothing completes (bounded waits
 // record a timeout in *status; *returned counts the threads that returned).
 cudaError_t launch_wait_selftest(int* status, int* returned, cudaStream_t st);

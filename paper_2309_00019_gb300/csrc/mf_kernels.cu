@@ -494,6 +494,27 @@ __global__ void k_compact_write(const unsigned long long* __restrict__ slots, in
 }
 
 
+// --- FP32 FMA throughput probe (context for the ALU roofline) -----------------
+
+// 8 independent FMA chains per thread, 16 x iters rounds; the result is
+// written only if it is exactly zero so the work cannot be removed.
+__global__ void __launch_bounds__(256) k_fma_probe(float* out, int iters, float a, float b) {
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (float)(threadIdx.x + i) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == 0.0f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // --- failure detection without a fault ----------------------------------------
 
 // One CTA waits on an mbarrier that no thread and no copy ever completes: every
@@ -625,6 +646,12 @@ __global__ void k_quant_bank(const float2* __restrict__ src, int64_t ld_src, int
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t st) {
+  k_fma_probe<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+  ++g_launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wait_selftest(int* status, int* returned, cudaStream_t st) {
   k_wait_selftest<<<1, 128, 0, st>>>(status, returned);

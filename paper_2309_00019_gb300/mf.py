@@ -91,6 +91,7 @@ SIGNATURES = {
     "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mf_chisq": (C.c_int, [_P, C.c_int32, _P, _P]),
     "mf_psd_welch": (C.c_int, [C.c_double, C.c_int32, _I64, _P, _I64, _I64, _I64, C.c_int32, _P, _P]),
+    "mf_fma_probe": (C.c_int, [C.POINTER(C.c_double), _P]),
     "mf_far": (C.c_int, [_P, _I64, _P, _I64, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P]),
     "mf_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(mf_batch_desc)]),
     "mf_batch_destroy": (None, [_P]),
@@ -499,3 +500,10 @@ def psd_welch(strain, fs, seg_len, stride, average="median", out=None, stream=No
     _check(None, load().mf_psd_welch(float(fs), n_det, n_samples, _ptr(strain), ld, seg_len, stride,
                                      0 if average == "mean" else 1, _ptr(out), stream))
     return out
+
+
+def fma_probe(stream=None):
+    """Measured FP32 FMA throughput of the device, TFLOP/s (mf_fma_probe)."""
+    t = C.c_double()
+    _check(None, load().mf_fma_probe(C.byref(t), stream))
+    return t.value
