@@ -152,7 +152,7 @@ mf_status mf_set_data_dtype(mf_plan_t plan, mf_dtype dtype);
 mf_status mf_set_row_valid(mf_plan_t plan, const int64_t* range);
 
 /* Templates per pass-1/pass-2 launch pair (the batch; default: as many as
- * fit a 256 MB intermediate).  Reallocates the intermediate (batch x n_det x
+ * fit a 1 GB intermediate).  Reallocates the intermediate (batch x n_det x
  * N x 8 bytes).  Errors: MF_EINVAL (batch < 1), MF_ENOMEM. */
 mf_status mf_set_batch(mf_plan_t plan, int32_t batch);
 

@@ -284,9 +284,10 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
   p->nb = d.n / 2 + 1;
   p->n_win = (d.n + d.window - 1) / d.window;
   p->ld_q = (p->nb + 63) / 64 * 64;
-  // batch of templates per pass pair: keep the pass-1 -> pass-2 scratch within ~64 MB (L2 resident)
+  // templates per pass pair: as many as fit a 1 GB pass-1 -> pass-2 intermediate (fewer, longer
+  // launches; the intermediate does not stay in L2 at any size that keeps launches efficient)
   const int64_t per = (int64_t)d.n_det * d.n * (int64_t)sizeof(float2);
-  int64_t budget = int64_t(256) << 20;
+  int64_t budget = int64_t(1024) << 20;
   if (const char* b = std::getenv("MF_SCRATCH_MB")) budget = std::max<int64_t>(1, std::atoll(b)) << 20;
   p->batch = (int)std::max<int64_t>(1, std::min<int64_t>(budget / per, 4096));
   const int64_t scratch_series = p->batch;
