@@ -43,8 +43,10 @@ KERNEL_NAMES = {2: ("k_cols", "k_rows")}
 
 
 def measured_traffic(kernel, series_per_launch):
-    """DRAM bytes per launch of `kernel` from the committed ncu summaries
-    (lines 'bench-traffic: <kernel> series=<s> dram_bytes=<b>'), or None."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries (lines
+    'bench-traffic: <kernel> series=<s> dram_bytes=<b>'), scaled from the captured
+    launch's s series to this launch's series (the traffic of these kernels grows in
+    proportion to the series they process), or None."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
@@ -56,8 +58,9 @@ def measured_traffic(kernel, series_per_launch):
             for line in fh:
                 if line.startswith("bench-traffic:"):
                     f = line.split()
-                    if f[1] == name and int(f[2].split("=")[1]) == int(round(series_per_launch)):
-                        return int(f[3].split("=")[1])
+                    if f[1] == name:
+                        series = int(f[2].split("=")[1])
+                        return int(f[3].split("=")[1]) * float(series_per_launch) / series
     return None
 
 
