@@ -52,6 +52,7 @@ struct mf_plan_s {
   int chisq_p = 0;
   float2* scratch = nullptr;
   int batch = 1;
+  CUtensorMap scratch_map{};  // pass-2 view of the scratch (mf::encode_scratch_map)
   unsigned long long* slots = nullptr;
   int64_t slots_cap = 0;        // in slots
   int32_t* sel_copy = nullptr;  // the selection of the last filter (device copy)
@@ -304,6 +305,11 @@ mf_status mf_plan(mf_plan_t* out, const mf_plan_desc* desc) {
     mf_destroy(p);
     return s;
   }
+  if (mf::encode_scratch_map(d.n, p->scratch, scratch_series * d.n_det, &p->scratch_map) != cudaSuccess) {
+    g_err = "mf_plan: tensor map of the scratch";
+    mf_destroy(p);
+    return MF_ECUDA;
+  }
   cudaMemsetAsync(p->count, 0, sizeof(int64_t), p->st);
   cudaMemsetAsync(p->status, 0, sizeof(int), p->st);
   if (mf::launch_fill_twiddles(d.n, p->tw, p->tw + 1024, p->st) != cudaSuccess ||
@@ -500,6 +506,8 @@ mf_status mf_set_batch(mf_plan_t p, int32_t batch) {
   mf_status s = dalloc(p, &p->scratch, (size_t)series * per, "scratch");
   if (s != MF_OK) return s;
   p->batch = batch;
+  if (mf::encode_scratch_map(p->d.n, p->scratch, series * p->d.n_det, &p->scratch_map) != cudaSuccess)
+    return fail(p, MF_ECUDA, "mf_set_batch: tensor map of the scratch");
   return MF_OK;
 }
 
@@ -612,7 +620,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
     e = mf::launch_filter2_pass1(a, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 1");
     if (prof) cudaEventRecord(p->ev[e0 + 1], p->st);
-    e = mf::launch_filter2_pass2(a, p->st);
+    e = mf::launch_filter2_pass2(a, p->scratch_map, p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter pass 2");
     if (prof) {
       cudaEventRecord(p->ev[e0 + 2], p->st);

@@ -11,12 +11,13 @@
 //           read; N1-point column transforms, each column owned by one group
 //           of T threads inside a warp (its exchange needs only a warp
 //           barrier); the four-step twiddle exp(+2 pi i j1 k2 / N); stores to
-//           the scratch in panels of P = RW rows: element (j1, k2) of a series
-//           at (j1 / P) N2 P + k2 P + j1 % P, so P consecutive threads fill
-//           whole sectors and a pass-2 item is one contiguous panel.
-//   k_rows: item = one panel (RW rows j1), one 1-D bulk copy; N2-point row
-//           transforms; rho^2 = |z|^2 / sigma^2 of z[j1 + N1 j2], threshold
-//           and window maxima in registers.
+//           the scratch in panels of P = max(T(N1) / 2, RW(N2)) rows:
+//           element (j1, k2) of a series at (j1 / P) N2 P + k2 P + j1 % P,
+//           so that a warp's store covers whole 128-byte lines.
+//   k_rows: item = RW rows j1 of one panel, brought in by a 3-D tensor-map
+//           copy (RW of the panel's P values at each k2; one 1-D bulk copy
+//           when RW = P); N2-point row transforms; rho^2 = |z|^2 / sigma^2 of
+//           z[j1 + N1 j2], threshold and window maxima in registers.
 // Sub-FFT twiddles come from a per-CTA shared table.  All mbarrier waits are
 // bounded (see mf_tma.cuh) and report through the plan's status word.
 // Programmatic dependent launch: each kernel lets the next one launch only
@@ -136,6 +137,21 @@ struct RowGeo {
   static constexpr int SMEM = BAR_OFF + 32;
 };
 
+// Panel height P of the pass-1 -> pass-2 scratch.  A pass-1 warp stores, per
+// instruction, T(N1) consecutive j1 of 32 / T(N1) consecutive columns k2; with
+// P >= T/2 those are whole 128-byte lines of at most two panels.  P is also a
+// multiple of the rows of one pass-2 item (RW(N2)), which are contiguous when
+// P = RW.
+template <int N1, int N2>
+struct ScratchGeo {
+  static constexpr int RA = SubFft<N1>::RA;
+  static constexpr int RW = RowGeo<N2>::RW;
+  static constexpr int HT = SubFft<N1>::T / 2;
+  static constexpr int P = HT > RW ? HT : RW;
+  static constexpr int BOXY = N2 < 256 ? N2 : 256;  // k2 per tensor-map box (256 at most)
+  static_assert(P % RW == 0 && N1 % P == 0 && N2 % BOXY == 0, "scratch panel geometry");
+};
+
 template <int BT>
 __device__ __forceinline__ float2 smem_h(const unsigned char* base, int idx) {
   if constexpr (BT == kBankF32) {
@@ -168,7 +184,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
   constexpr int NCB = N2 / C;
   constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
-  constexpr int PH = RowGeo<N2>::RW;  // scratch panel height
+  constexpr int PH = ScratchGeo<N1, N2>::P;  // scratch panel height
   extern __shared__ __align__(128) unsigned char sm[];
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: tiles of the slot landed
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
       const float2* twr = a.tw4 + (int64_t)k2 * (RA + 1);
       float2 w = __ldg(twr + j);
       const float2 st = __ldg(twr + RA);
-      if constexpr (RA % PH == 0) {  // j + q RA stays in j's panel row: one base, constant panel steps
+      if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
         float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
@@ -295,12 +311,15 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
 // pass 2
 // ---------------------------------------------------------------------------
 
+// tm: the scratch as [series * N1 / PH panels][N2][PH] of 8-byte values, box
+// {RW, BOXY, 1} (unused when RW = PH: an item is then one contiguous panel)
 template <int N1, int N2>
-__global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
+__global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtensorMap tm, FilterArgs a) {
   using G = SubFft<N2>;
   using P = RowGeo<N2>;
   using X = typename P::X;
-  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW;
+  using SG = ScratchGeo<N1, N2>;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW, PH = SG::P;
   constexpr int NRB = N1 / RW;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -320,8 +339,16 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(FilterArgs a) {
   auto issue = [&](int item, int slot) {
     const int s = item / NRB, j10 = (item % NRB) * RW;
     mbar_expect_tx(bar + slot, (uint32_t)(P::ITEM * 8));
-    bulk_g2s_hint(sm + slot * P::SLOT, a.scratch + (int64_t)s * N + (int64_t)j10 * N2, (uint32_t)(P::ITEM * 8),
-                  bar + slot, pol_last_use);
+    if constexpr (RW == PH) {
+      bulk_g2s_hint(sm + slot * P::SLOT, a.scratch + (int64_t)s * N + (int64_t)j10 * N2, (uint32_t)(P::ITEM * 8),
+                    bar + slot, pol_last_use);
+    } else {
+      // rows j10 .. j10 + RW - 1 of panel j10 / PH: RW * 8 bytes at each k2, landing as [k2][row]
+      const int z = s * (N1 / PH) + j10 / PH;
+#pragma unroll
+      for (int y = 0; y < N2; y += SG::BOXY)
+        tma_load_3d_hint(sm + slot * P::SLOT + (size_t)y * RW * 8, &tm, j10 % PH, y, z, bar + slot, pol_last_use);
+    }
   };
   if (tid == 0) {
     mbar_expect_tx(bar + 2, (uint32_t)P::TW_BYTES);
@@ -442,7 +469,7 @@ cudaError_t run_cols_bt(const FilterArgs& a, cudaStream_t st) {
 }
 
 template <int N1, int N2>
-cudaError_t run_rows(const FilterArgs& a, cudaStream_t st) {
+cudaError_t run_rows(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
   using P = RowGeo<N2>;
   static_assert(P::SMEM * 3 <= 230400, "k_rows: three CTAs per SM must fit in shared memory");
   auto k = k_rows<N1, N2>;
@@ -453,9 +480,43 @@ cudaError_t run_rows(const FilterArgs& a, cudaStream_t st) {
     attr = true;
   }
   const int items = a.count * a.n_det * (N1 / P::RW);
-  cudaError_t e = launch_pdl(k, grid2(items), kT2, P::SMEM, st, a);
+  cudaError_t e = launch_pdl(k, grid2(items), kT2, P::SMEM, st, tm, a);
   add_launches(1);
   return e;
+}
+
+// signature of the driver's cuTensorMapEncodeTiled (CUDA 12.0 ABI), fetched at run time
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+template <int N1, int N2>
+cudaError_t encode_scratch_of(const float2* scratch, int64_t series, CUtensorMap* m) {
+  using SG = ScratchGeo<N1, N2>;
+  *m = CUtensorMap{};
+  if (SG::RW == SG::P) return cudaSuccess;  // contiguous items: no tensor map
+  auto fn = encode_fn();
+  if (!fn || !scratch || series < 1) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)SG::P, (cuuint64_t)N2, (cuuint64_t)(series * (N1 / SG::P))};
+  cuuint64_t strides[2] = {(cuuint64_t)SG::P * 8, (cuuint64_t)N2 * SG::P * 8};
+  cuuint32_t box[3] = {(cuuint32_t)SG::RW, (cuuint32_t)SG::BOXY, 1u};
+  cuuint32_t es[3] = {1u, 1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(scratch), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 #define MF_DISPATCH2(n, FN, ARGS)            \
@@ -506,7 +567,13 @@ cudaError_t tw4_count_of(int64_t* c) {
 
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH2(a.n, run_cols_bt, (a, st)) }
 
-cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH2(a.n, run_rows, (a, st)) }
+cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
+  MF_DISPATCH2(a.n, run_rows, (a, tm, st))
+}
+
+cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m) {
+  MF_DISPATCH2(n, encode_scratch_of, (scratch, series, m))
+}
 
 cudaError_t launch_fill_tw4(int64_t n, float2* tw4, cudaStream_t st) { MF_DISPATCH2(n, run_fill_tw4, (tw4, st)) }
 

@@ -84,7 +84,10 @@ bool plan_capturable(const ::mf_plan_s* p);
 // weighted data are in column layout: element k = k1 N2 + k2 of the non-zero
 // half (k1 < N1/2) at k2 N1/2 + k1 (see launch_to_cols).
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
-cudaError_t launch_filter2_pass2(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& scratch_map, cudaStream_t st);
+// Tensor map of the pass-1 -> pass-2 scratch (`series` series of length n)
+// through which pass 2 reads its items; all zero where pass 2 needs none.
+cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m);
 cudaError_t launch_fill_twiddles(int64_t n, float2* tw1, float2* tw2, cudaStream_t st);
 // four-step twiddles of k_cols by column: tw4[k2 (RA + 1) + j] = w_N^{j k2}, j <= RA(N1), k2 < N2;
 // tw4_count(n) entries
