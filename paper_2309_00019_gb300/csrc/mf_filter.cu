@@ -3,7 +3,8 @@
 // N = N1 N2 four-step transform on sm_103a: 128-thread CTAs, three per SM,
 // each a persistent loop over work items whose inputs are brought into shared
 // memory by the bulk-copy (TMA) engine while the previous item computes.
-//   k_cols: item = C columns k2 of one (template, detector) series.  The
+//   k_cols: item = C columns k2 of one (template, detector) series, the
+//           detector fastest in the item order.  The
 //           template bank and the weighted data are stored column-major over
 //           the non-zero half (element k = k1 N2 + k2, k1 < N1/2, at
 //           k2 N1/2 + k1), so an item's two tiles are two contiguous 1-D bulk
@@ -205,7 +206,6 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     // producer warp: one lane issues every item's tiles into the slot its consumers released
     if (tid == kColConsumers) {
       const unsigned char* qbase = static_cast<const unsigned char*>(QT == kBankF32 ? (const void*)a.q : a.q_lp);
-      const uint64_t pol_stream = policy_evict_first();
       mbar_expect_tx(twb, (uint32_t)P::TW_BYTES);
       bulk_g2s(sm + P::TW_OFF, a.tw1, (uint32_t)P::TW_BYTES, twb);
       // the weighted data come from the kernel just before only for the first batch; otherwise
@@ -220,16 +220,18 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
         const int slot = k & 1;
         if (k >= 2 && !(ok = mbar_wait_bounded(empty + slot, (uint32_t)(((k >> 1) + 1) & 1), a.status))) break;
         fence_proxy_async();
-        const int s = item / NCB, cb = item % NCB;
-        const int b = s / a.n_det, d = s % a.n_det;
+        // detector fastest: the n_det items of one bank tile are issued back to back, so the
+        // tile is read from HBM once and from L2 for the other detectors
+        const int d = item % a.n_det, cb = (item / a.n_det) % NCB, b = item / (a.n_det * NCB);
         const int64_t tmpl = a.sel[a.pos0 + b];
         unsigned char* dst = sm + slot * P::SLOT;
         mbar_expect_tx(full + slot, (uint32_t)(C * (P::H_COL + P::Q_COL)));
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const int64_t col = (int64_t)cb * C + c;
-          bulk_g2s_hint(dst + c * S * 8, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + col * R) * P::HB,
-                        (uint32_t)P::H_COL, full + slot, pol_stream);
+          // default L2 priority: the n_det - 1 later items of this tile read it from L2
+          bulk_g2s(dst + c * S * 8, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + col * R) * P::HB,
+                   (uint32_t)P::H_COL, full + slot);
           bulk_g2s(dst + c * S * 8 + P::H_COL, qbase + ((int64_t)d * a.ld_q + col * R) * P::QB, (uint32_t)P::Q_COL,
                    full + slot);
         }
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     const int slot = k & 1;
     if (!mbar_wait_bounded(full + slot, (uint32_t)((k >> 1) & 1), a.status)) break;
     const unsigned char* col = sm + slot * P::SLOT + ca * S * 8;
-    const int s = item / NCB;
+    const int s = (item / (a.n_det * NCB)) * a.n_det + item % a.n_det;
     float2 v[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
     __syncwarp();
     float2* out = a.scratch + (int64_t)s * N;
-    const int k2 = (item % NCB) * C + ca;
+    const int k2 = ((item / a.n_det) % NCB) * C + ca;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = ta + T * i;
@@ -327,7 +329,9 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);
   const int tid = threadIdx.x;
   const int row = tid % RW, t = tid / RW;  // rows fastest: the panel is [k2][row]
-  const int n_items = a.count * a.n_det * NRB;
+  // series in reverse order: the last ones pass 1 wrote are the likeliest to be still in L2
+  const int n_series = a.count * a.n_det;
+  const int n_items = n_series * NRB;
   if (tid == 0) {
     mbar_init(bar + 0, 1);
     mbar_init(bar + 1, 1);
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
   __syncthreads();
   const uint64_t pol_last_use = policy_evict_first();
   auto issue = [&](int item, int slot) {
-    const int s = item / NRB, j10 = (item % NRB) * RW;
+    const int s = n_series - 1 - item / NRB, j10 = (item % NRB) * RW;
     mbar_expect_tx(bar + slot, (uint32_t)(P::ITEM * 8));
     if constexpr (RW == PH) {
       bulk_g2s_hint(sm + slot * P::SLOT, a.scratch + (int64_t)s * N + (int64_t)j10 * N2, (uint32_t)(P::ITEM * 8),
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
     const int slot = k & 1;
     const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
     const float2* stage = reinterpret_cast<const float2*>(sm + slot * P::SLOT);
-    const int s = item / NRB;
+    const int s = n_series - 1 - item / NRB;
     const int j1 = (item % NRB) * RW + row;
     float2 v[RA];
 #pragma unroll
