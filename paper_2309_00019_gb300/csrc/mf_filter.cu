@@ -245,7 +245,6 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   }
   // consumer warps: column ca of every item, T threads per column
   const int ca = tid / T, ta = tid % T;
-  const uint64_t pol_keep = policy_evict_last();
   pdl_wait();  // the previous kernel (reader of the scratch we are about to write) has completed
   if (!mbar_wait_bounded(twb, 0, a.status)) return;
   int k = 0;
@@ -289,14 +288,14 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
         float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
-          st_global_hint(ob + (int64_t)q * (RA / PH) * (N2 * PH), cmul(u[q], w), pol_keep);
+          ob[(int64_t)q * (RA / PH) * (N2 * PH)] = cmul(u[q], w);
           if (q + 1 < RB) w = cmul(w, st);
         }
       } else {
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
           const int j1 = j + q * RA;
-          st_global_hint(out + (int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH), cmul(u[q], w), pol_keep);
+          out[(int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH)] = cmul(u[q], w);
           if (q + 1 < RB) w = cmul(w, st);
         }
       }
