@@ -63,6 +63,7 @@ class mf_batch_trigger(C.Structure):
 
 
 MF_RUN_SERIAL, MF_RUN_STREAMS, MF_RUN_GRAPH = 0, 1, 2
+MF_FILTER_TWO_PASS, MF_FILTER_FUSED = 0, 1
 BATCH_TRIGGER_NP = np.dtype([("det", np.int32), ("cls", np.int32), ("tmpl", np.int32), ("reserved", np.int32),
                              ("sample", np.int64), ("snr", np.float32), ("phase", np.float32)])
 
@@ -105,6 +106,7 @@ SIGNATURES = {
     "mf_batch_run": (C.c_int, [_P, _P, _I64, C.c_int32]),
     "mf_batch_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
     "mf_set_batch": (C.c_int, [_P, C.c_int32]),
+    "mf_set_filter_mode": (C.c_int, [_P, C.c_int32]),
     "mf_strain_to_fd": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_decimate": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_filter": (C.c_int, [_P, _P, _I64, _P, _I64]),
@@ -262,6 +264,10 @@ class Plan:
 
     def set_batch(self, batch):
         _check(self.h, self.lib.mf_set_batch(self.h, batch))
+
+    def set_filter_mode(self, mode):
+        """MF_FILTER_FUSED (default) or MF_FILTER_TWO_PASS (see mf_set_filter_mode)."""
+        _check(self.h, self.lib.mf_set_filter_mode(self.h, int(mode)))
 
     def sigmasq(self, n=None):
         n = self.n_tmpl if n is None else n
