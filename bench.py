@@ -78,13 +78,10 @@ def parse():
                     help="instead of the benchmark, run two mf_filter calls on a 2-detector plan with N = 2^LOG2N "
                          "(a small, fixed case for profiler captures) and exit")
     ap.add_argument("--kernel-templates", type=int, default=16)
-    ap.add_argument("--fused", action="store_true",
-                    help="filter each selection in one launch of both passes (MF_FILTER_FUSED) instead of one "
-                         "pass-1 and one pass-2 launch per template batch")
     return ap.parse_args()
 
 
-def kernel_case(lg, n_tmpl, fused=False):
+def kernel_case(lg, n_tmpl):
     """Two filter calls of a 2-detector, n_tmpl-template plan at N = 2^lg (TaylorF2 bank,
     coloured noise); used as the fixed workload of profiler captures."""
     import torch
@@ -102,7 +99,6 @@ def kernel_case(lg, n_tmpl, fused=False):
     bank = synth.taylorf2_torch(n, fs, m1, m2, 30.0, dev)
     fd = np.stack([synth.coloured_noise_fd(rng, n, fs) for _ in range(2)]).astype(np.complex64)
     p = mf.Plan(fs, n, 2, 30.0, fs / 2, 4.0, int(fs))
-    p.set_filter_mode(mf.MF_FILTER_FUSED if fused else mf.MF_FILTER_TWO_PASS)
     p.set_psd(synth.psd_bins(n, fs))
     p.load_bank(bank)
     d = torch.from_numpy(fd).to(dev)
@@ -247,7 +243,7 @@ def reference_arm(args, rank, world):
 def main():
     args = parse()
     if args.kernel_case:
-        return kernel_case(args.kernel_case, args.kernel_templates, args.fused)
+        return kernel_case(args.kernel_case, args.kernel_templates)
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
@@ -273,9 +269,6 @@ def main():
     hp = HierParams.from_config(cfg)
     h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), cfg.nbhd_ptr, cfg.nbhd_idx,
                   device=dev)
-    if args.fused:
-        for p in (h.p1, h.p2):
-            p.set_filter_mode(mf.MF_FILTER_FUSED)
     for r0, rows in synth.taylorf2_chunks_torch(cfg.n1, cfg.fs1, cfg.coarse_m1, cfg.coarse_m2, cfg.f_low, dev,
                                                 chunk=256, ld=h.ld1):
         h.set_bank_rows(1, r0, rows)
@@ -344,10 +337,6 @@ def main():
                                   launches=s[f"{k}_launches"], series=s[f"{k}_series"],
                                   flops_series=5.0 * n * math.log2(sub), n=n,
                                   tmpl_bytes_series=(nb * 8 / hp.n_det) if k == "pass1" else 0.0))
-        if s["fused_launches"] > 0:  # both passes in one launch: 5 N log2 N per series
-            kinds.append(dict(kernel=f"k_fused<{n1s}> ({stage})", ms=s["fused_ms"], launches=s["fused_launches"],
-                              series=s["fused_series"], flops_series=5.0 * n * math.log2(n), n=n,
-                              tmpl_bytes_series=nb * 8 / hp.n_det))
     dom = max(kinds, key=lambda d: d["ms"]) if kinds else None
     roof = None
     hbm_gbs, hbm_kind = peaks()

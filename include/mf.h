@@ -147,31 +147,14 @@ mf_status mf_set_data_dtype(mf_plan_t plan, mf_dtype dtype);
  * longer data (Sec. V.C: the data are analysed in overlapping segments): row
  * d keeps only samples in [range[2d], range[2d+1]) (host int64 [2 n_det],
  * 0 <= begin <= end <= N; copied), replacing the plan's valid range for
- * every row; NULL restores it.  Errors: MF_EINVAL, MF_ENOMEM. */
+ * every row; NULL restores it.  Plans built with another filter
+ * implementation switch to the TMA-staged one.  Errors: MF_EINVAL, MF_ENOMEM. */
 mf_status mf_set_row_valid(mf_plan_t plan, const int64_t* range);
 
 /* Templates per pass-1/pass-2 launch pair (the batch; default: as many as
  * fit a 1 GB intermediate).  Reallocates the intermediate (batch x n_det x
  * N x 8 bytes).  Errors: MF_EINVAL (batch < 1), MF_ENOMEM. */
 mf_status mf_set_batch(mf_plan_t plan, int32_t batch);
-
-/* Launch shape of mf_filter's transform (Sec. V.C: one inverse FFT per
- * template and segment, here a four-step N1 x N2 transform in two passes).
- * MF_FILTER_TWO_PASS (the default): every batch of templates takes one pass-1
- * and one pass-2 launch through the intermediate in HBM.
- * MF_FILTER_FUSED: at N = 2^18 and 2^20 with a batch of at least
- * 2 templates, both passes of the whole selection run in one persistent
- * launch.  Each SM takes the pass-1 or the pass-2 role; the intermediate is a
- * ring of min(batch, max(4, 64 MB / (n_det N 8 bytes))) templates that stays
- * in L2, and per-template completion counters order the passes (bounded
- * waits, reported through the plan status; the launch needs CTAs on at least
- * two SMs); elsewhere it falls back to the two-pass shape.  It keeps the
- * intermediate out of HBM but is slower on GB300 than the two-pass shape.
- * Both shapes compute the same arithmetic and give identical triggers.
- * Errors: MF_EINVAL. */
-#define MF_FILTER_TWO_PASS 0
-#define MF_FILTER_FUSED 1
-mf_status mf_set_filter_mode(mf_plan_t plan, int32_t mode);
 
 /* sigma_t^2 of templates 0..n-1 (float64, Eq. 2) into host out[n]; synchronises. */
 mf_status mf_get_sigmasq(mf_plan_t plan, double* out, int64_t n);
@@ -218,18 +201,15 @@ mf_status mf_device_triggers(mf_plan_t plan, const mf_trigger** trig, const int6
  * the plan's stream (up to 1024 batches between reads): pass1_* is the
  * product + column-transform kernel, pass2_* the row-transform + SNR /
  * threshold / window-max kernel; *_series = (template, detector) series they
- * processed, *_ms = summed device time; fused_* the same for the persistent
- * kernel that runs both passes of all batches of one mf_filter in one launch. */
+ * processed, *_ms = summed device time. */
 typedef struct {
   int64_t launches;
   int64_t pass1_launches, pass1_series;
   double pass1_ms;
   int64_t pass2_launches, pass2_series;
   double pass2_ms;
-  int64_t fused_launches, fused_series;  /* single-launch filter (both passes, every batch) */
-  double fused_ms;
-  int32_t impl;       /* filter kernels in use: 2 one pass-1 and one pass-2 launch per batch, 3 one fused launch */
-  int32_t batch;      /* templates per pass pair (impl 2); it bounds the fused launch's ring (impl 3) */
+  int32_t impl;       /* filter kernels in use: 2 = TMA-staged k_cols / k_rows (the only ones) */
+  int32_t batch;      /* templates per pass-1 / pass-2 launch pair */
 } mf_plan_stats;
 
 /* Turn event profiling of the filter kernels on (enable != 0) or off. */

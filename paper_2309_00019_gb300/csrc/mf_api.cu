@@ -53,9 +53,6 @@ struct mf_plan_s {
   float2* scratch = nullptr;
   int batch = 1;
   CUtensorMap scratch_map{};  // pass-2 view of the scratch (mf::encode_scratch_map)
-  int filter_mode = MF_FILTER_TWO_PASS;  // or MF_FILTER_FUSED: one launch where supported
-  unsigned* fz_ctr = nullptr;         // fused kernel: queue, per-unit completion counters
-  int64_t fz_cap = 0;                 // in units
   unsigned long long* slots = nullptr;
   int64_t slots_cap = 0;        // in slots
   int32_t* sel_copy = nullptr;  // the selection of the last filter (device copy)
@@ -91,17 +88,10 @@ struct mf_plan_s {
   std::vector<cudaEvent_t> ev;      // pool, 3 per sampled batch
   struct Sample {
     int e0;
-    int64_t series;  // < 0: one launch of both passes (the fused kernel) over -series series
+    int64_t series;
   };
   std::vector<Sample> samples;      // batch samples awaiting read
 };
-
-namespace {
-// mf_filter runs both passes in one launch: requested, supported at this N, and a scratch ring that fits
-bool uses_fused(const mf_plan_s* p) {
-  return p->filter_mode == MF_FILTER_FUSED && mf::fused_supported(p->d.n) && p->batch >= 2;
-}
-}  // namespace
 
 namespace mf {
 int64_t plan_templates(const mf_plan_s* p) { return p ? p->n_tmpl : 0; }
@@ -121,15 +111,12 @@ uint64_t plan_fingerprint(const mf_plan_s* p) {
   mix((uint64_t)(uintptr_t)p->row_valid);
   mix((uint64_t)(uintptr_t)p->scratch);
   mix((uint64_t)(uintptr_t)p->slots);
-  mix((uint64_t)p->filter_mode);
-  mix((uint64_t)(uintptr_t)p->fz_ctr);
   return h;
 }
 
 bool plan_capturable(const mf_plan_s* p) {
   if (!p || !p->scale_valid || p->prof) return false;
   const int64_t need = (int64_t)p->d.n_det * p->n_tmpl * p->n_win;
-  if (uses_fused(p) && p->fz_cap < p->n_tmpl) return false;
   return p->slots_cap >= need && p->sel_cap >= p->n_tmpl && p->bc_cap >= mf::compact_blocks(need);
 }
 }  // namespace mf
@@ -343,7 +330,6 @@ void mf_destroy(mf_plan_t p) {
   dfree(p->count); dfree(p->bc); dfree(p->coincs); dfree(p->n_coinc); dfree(p->maxrho); dfree(p->nb_ptr);
   dfree(p->q_lp); dfree(p->dmax); dfree(p->dscale); dfree(p->row_valid); dfree(p->bpow); dfree(p->edges);
   dfree(p->nb_idx); dfree(p->flags); dfree(p->ubc); dfree(p->ucount); dfree(p->status); dfree(p->tw); dfree(p->tw4);
-  dfree(p->fz_ctr);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
 }
@@ -525,13 +511,6 @@ mf_status mf_set_batch(mf_plan_t p, int32_t batch) {
   return MF_OK;
 }
 
-mf_status mf_set_filter_mode(mf_plan_t p, int32_t mode) {
-  if (!p) return fail(p, MF_EINVAL, "mf_set_filter_mode: null plan");
-  if (mode != MF_FILTER_FUSED && mode != MF_FILTER_TWO_PASS) return fail(p, MF_EINVAL, "mf_set_filter_mode: mode");
-  p->filter_mode = mode;
-  return MF_OK;
-}
-
 mf_status mf_load_bank(mf_plan_t p, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld, const float* scales,
                        int on_device) {
   if (!p || !htilde) return fail(p, MF_EINVAL, "mf_load_bank: null argument");
@@ -631,32 +610,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.dscale = p->dscale;
   LaunchScope ls(p);
   ls.before = launches_before;
-  if (uses_fused(p)) {
-    const size_t words = (size_t)mf::fused_counter_words(n_sel);
-    if (p->fz_cap < n_sel) {
-      mf_status s = dalloc(p, &p->fz_ctr, words * sizeof(unsigned), "fused-kernel counters");
-      if (s != MF_OK) return s;
-      p->fz_cap = n_sel;
-    }
-    e = cudaMemsetAsync(p->fz_ctr, 0, words * sizeof(unsigned), p->st);
-    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter counters");
-    a.pos0 = 0;
-    a.first_batch = 1;
-    a.count = (int)n_sel;
-    const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
-    const int e0 = prof ? (int)p->samples.size() * 3 : 0;
-    if (prof) cudaEventRecord(p->ev[e0], p->st);
-    const int64_t unit_bytes = (int64_t)p->d.n_det * p->d.n * (int64_t)sizeof(float2);
-    const int ring = (int)std::min<int64_t>(p->batch, std::max<int64_t>(4, mf::kFusedRingBytes / unit_bytes));
-    e = mf::launch_filter_fused(a, p->scratch_map, p->fz_ctr, (int)n_sel, ring, p->st);
-    if (e != cudaSuccess) return cuda_fail(p, e, "mf_filter fused kernel");
-    if (prof) {
-      cudaEventRecord(p->ev[e0 + 1], p->st);
-      cudaEventRecord(p->ev[e0 + 2], p->st);
-      p->samples.push_back({e0, -n_sel * p->d.n_det});
-    }
-  }
-  for (int64_t pos0 = 0; !uses_fused(p) && pos0 < n_sel; pos0 += p->batch) {
+  for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
     a.pos0 = pos0;
     a.first_batch = pos0 == 0 ? 1 : 0;
     a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
@@ -704,12 +658,6 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     e = cudaEventElapsedTime(&t1, p->ev[sm.e0], p->ev[sm.e0 + 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, p->ev[sm.e0 + 1], p->ev[sm.e0 + 2]);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_stats elapsed");
-    if (sm.series < 0) {  // the fused kernel: both passes in one launch
-      p->stats.fused_launches += 1;
-      p->stats.fused_series += -sm.series;
-      p->stats.fused_ms += t1;
-      continue;
-    }
     p->stats.pass1_launches += 1;
     p->stats.pass1_series += sm.series;
     p->stats.pass1_ms += t1;
@@ -718,7 +666,7 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     p->stats.pass2_ms += t2;
   }
   p->samples.clear();
-  p->stats.impl = uses_fused(p) ? 3 : 2;
+  p->stats.impl = 2;
   p->stats.batch = p->batch;
   *out = p->stats;
   if (reset) p->stats = mf_plan_stats{};

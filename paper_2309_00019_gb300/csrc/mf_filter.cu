@@ -25,8 +25,6 @@
 // when a CTA has finished all its items, so the next kernel's CTAs (which wait
 // for this one to complete before touching the scratch) take the slots of
 // retiring CTAs instead of competing with this kernel's own CTAs for them.
-#include <algorithm>
-
 #include "mf_common.cuh"
 #include "mf_tma.cuh"
 
@@ -147,6 +145,7 @@ struct RowGeo {
 // P = RW.
 template <int N1, int N2>
 struct ScratchGeo {
+  static constexpr int RA = SubFft<N1>::RA;
   static constexpr int RW = RowGeo<N2>::RW;
   static constexpr int HT = SubFft<N1>::T / 2;
   static constexpr int P = HT > RW ? HT : RW;
@@ -175,113 +174,18 @@ __global__ void k_fill_twiddles(float2* tw) {
   }
 }
 
-// Pass-1 work on one column: its T threads (ta) read the column's template and
-// data tiles from region colr, form x = q conj(h), transform over k1 (upper
-// half zero), reuse the region as the column's exchange buffer, apply the
-// four-step twiddle w_N^{j1 k2} and store to the panels of series `out`.
-template <int N1, int N2, int BT, int QT>
-__device__ __forceinline__ void cols_column(unsigned char* colr, const float2* tw, const float2* tw4, float2* out, int k2,
-                                            int ta) {
-  using G = SubFft<N1>;
-  using P = ColGeo<N1, BT, QT>;
-  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB;
-  constexpr int PH = ScratchGeo<N1, N2>::P;  // scratch panel height
-  float2 v[RA];
-#pragma unroll
-  for (int r = 0; r < RA; ++r) {
-    if (r >= RA / 2) {
-      v[r] = make_float2(0.f, 0.f);
-    } else {
-      const int idx = ta + r * RB;  // k1 < N1/2
-      v[r] = cmulc(smem_h<QT>(colr + P::H_COL, idx), smem_h<BT>(colr, idx));
-    }
-  }
-  __syncwarp();  // the column's tiles are read: its region becomes the exchange buffer
-  dft<RA, true>(v);
-  float2* xb = reinterpret_cast<float2*>(colr);
-#pragma unroll
-  for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int j = ta + T * i;
-    float2 u[RB];
-    u[0] = xb[j];
-#pragma unroll
-    for (int r = 1; r < RB; ++r) u[r] = cmul(xb[j + r * RA + r], tw[r * RA + j]);
-    dft<RB>(u);
-    // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q; the table row of
-    // column k2 holds w_N^{j k2} for j <= RA, so a warp's loads are contiguous
-    const float2* twr = tw4 + (int64_t)k2 * (RA + 1);
-    float2 w = __ldg(twr + j);
-    const float2 st = __ldg(twr + RA);
-    if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
-      float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
-#pragma unroll
-      for (int q = 0; q < RB; ++q) {
-        ob[(int64_t)q * (RA / PH) * (N2 * PH)] = cmul(u[q], w);
-        if (q + 1 < RB) w = cmul(w, st);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < RB; ++q) {
-        const int j1 = j + q * RA;
-        out[(int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH)] = cmul(u[q], w);
-        if (q + 1 < RB) w = cmul(w, st);
-      }
-    }
-  }
-}
-
-// Pass-2 work on one item by the kT2 compute threads: rows j10 .. j10 + RW - 1
-// of series s, staged in slotp as [k2][row], to registers; after_read() (a
-// barrier of those threads, after which the stage may be overwritten; true =
-// abort); N2-point row transforms through the exchange buffer (xbar() between
-// its writes and reads); rho^2 threshold and window maxima (ep).
-template <int N1, int N2, class AfterRead, class XBar>
-__device__ __forceinline__ bool rows_item(unsigned char* slotp, const float2* tw, const RawEpi& ep, int s, int j10,
-                                          int tid, AfterRead after_read, XBar xbar) {
-  using G = SubFft<N2>;
-  using P = RowGeo<N2>;
-  using X = typename P::X;
-  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW;
-  const int row = tid % RW, t = tid / RW;  // rows fastest: the stage is [k2][row]
-  const float2* stage = reinterpret_cast<const float2*>(slotp);
-  const int j1 = j10 + row;
-  float2 v[RA];
-#pragma unroll
-  for (int r = 0; r < RA; ++r) v[r] = stage[(t + r * RB) * RW + row];
-  if (after_read()) return false;
-  dft<RA>(v);
-  float2* xb = reinterpret_cast<float2*>(slotp);
-#pragma unroll
-  for (int q = 0; q < RA; ++q) xb[X::idx(row, t * RA + q)] = v[q];
-  xbar();
-  const auto se = ep.series(s);
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int j = t + T * i;
-    float2 u[RB];
-    u[0] = xb[X::idx(row, j)];
-#pragma unroll
-    for (int r = 1; r < RB; ++r) u[r] = cmul(xb[X::idx(row, j + r * RA)], tw[r * RA + j]);
-    dft<RB>(u);
-#pragma unroll
-    for (int q = 0; q < RB; ++q) ep(se, (int64_t)j1 + (int64_t)N1 * (j + q * RA), u[q]);
-  }
-  return true;
-}
-
 // ---------------------------------------------------------------------------
 // pass 1
 // ---------------------------------------------------------------------------
 
 template <int N1, int N2, int BT, int QT>
 __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
+  using G = SubFft<N1>;
   using P = ColGeo<N1, BT, QT>;
-  constexpr int T = SubFft<N1>::T, C = P::C, R = P::R, S = P::S;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
   constexpr int NCB = N2 / C;
   constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
+  constexpr int PH = ScratchGeo<N1, N2>::P;  // scratch panel height
   extern __shared__ __align__(128) unsigned char sm[];
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: tiles of the slot landed
@@ -347,9 +251,55 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
     if (!mbar_wait_bounded(full + slot, (uint32_t)((k >> 1) & 1), a.status)) break;
+    const unsigned char* col = sm + slot * P::SLOT + ca * S * 8;
     const int s = (item / (a.n_det * NCB)) * a.n_det + item % a.n_det;
-    cols_column<N1, N2, BT, QT>(sm + slot * P::SLOT + ca * S * 8, tw, a.tw4, a.scratch + (int64_t)s * N,
-                                ((item / a.n_det) % NCB) * C + ca, ta);
+    float2 v[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+      if (r >= RA / 2) {
+        v[r] = make_float2(0.f, 0.f);
+      } else {
+        const int idx = ta + r * RB;  // k1 < N1/2
+        v[r] = cmulc(smem_h<QT>(col + P::H_COL, idx), smem_h<BT>(col, idx));
+      }
+    }
+    __syncwarp();  // the column's tiles are read: its region becomes the exchange buffer
+    dft<RA, true>(v);
+    float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT) + ca * S;
+#pragma unroll
+    for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
+    __syncwarp();
+    float2* out = a.scratch + (int64_t)s * N;
+    const int k2 = ((item / a.n_det) % NCB) * C + ca;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = ta + T * i;
+      float2 u[RB];
+      u[0] = xb[j];
+#pragma unroll
+      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[j + r * RA + r], tw[r * RA + j]);
+      dft<RB>(u);
+      // four-step twiddle w_N^{(j + q RA) k2} = w_N^{j k2} (w_N^{RA k2})^q; the table row of
+      // column k2 holds w_N^{j k2} for j <= RA, so a warp's loads are contiguous
+      const float2* twr = a.tw4 + (int64_t)k2 * (RA + 1);
+      float2 w = __ldg(twr + j);
+      const float2 st = __ldg(twr + RA);
+      if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
+        float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          ob[(int64_t)q * (RA / PH) * (N2 * PH)] = cmul(u[q], w);
+          if (q + 1 < RB) w = cmul(w, st);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const int j1 = j + q * RA;
+          out[(int64_t)(j1 / PH) * (N2 * PH) + k2 * PH + (j1 % PH)] = cmul(u[q], w);
+          if (q + 1 < RB) w = cmul(w, st);
+        }
+      }
+    }
     // this warp is done with the slot: order its shared accesses before the next bulk copy into it
     fence_proxy_async();
     __syncwarp();
@@ -366,15 +316,18 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
 // {RW, BOXY, 1} (unused when RW = PH: an item is then one contiguous panel)
 template <int N1, int N2>
 __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtensorMap tm, FilterArgs a) {
+  using G = SubFft<N2>;
   using P = RowGeo<N2>;
+  using X = typename P::X;
   using SG = ScratchGeo<N1, N2>;
-  constexpr int RW = P::RW, PH = SG::P;
+  constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, RW = P::RW, PH = SG::P;
   constexpr int NRB = N1 / RW;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char sm[];
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);
   const int tid = threadIdx.x;
+  const int row = tid % RW, t = tid / RW;  // rows fastest: the panel is [k2][row]
   // series in reverse order: the last ones pass 1 wrote are the likeliest to be still in L2
   const int n_series = a.count * a.n_det;
   const int n_items = n_series * NRB;
@@ -414,293 +367,36 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
   for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
     const int slot = k & 1;
     const bool fail = !mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), a.status);
+    const float2* stage = reinterpret_cast<const float2*>(sm + slot * P::SLOT);
     const int s = n_series - 1 - item / NRB;
-    const bool go = rows_item<N1, N2>(
-        sm + slot * P::SLOT, tw, ep, s, (item % NRB) * RW, tid,
-        [&]() {
-          if (__syncthreads_or(fail)) return true;
-          if (tid == 0 && item + (int)gridDim.x < n_items) {
-            fence_proxy_async();
-            issue(item + gridDim.x, slot ^ 1);
-          }
-          return false;
-        },
-        []() { __syncthreads(); });
-    if (!go) return;
+    const int j1 = (item % NRB) * RW + row;
+    float2 v[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) v[r] = stage[(t + r * RB) * RW + row];
+    if (__syncthreads_or(fail)) return;
+    if (tid == 0 && item + (int)gridDim.x < n_items) {
+      fence_proxy_async();
+      issue(item + gridDim.x, slot ^ 1);
+    }
+    dft<RA>(v);
+    float2* xb = reinterpret_cast<float2*>(sm + slot * P::SLOT);
+#pragma unroll
+    for (int q = 0; q < RA; ++q) xb[X::idx(row, t * RA + q)] = v[q];
+    __syncthreads();
+    const auto se = ep.series(s);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = t + T * i;
+      float2 u[RB];
+      u[0] = xb[X::idx(row, j)];
+#pragma unroll
+      for (int r = 1; r < RB; ++r) u[r] = cmul(xb[X::idx(row, j + r * RA)], tw[r * RA + j]);
+      dft<RB>(u);
+#pragma unroll
+      for (int q = 0; q < RB; ++q) ep(se, (int64_t)j1 + (int64_t)N1 * (j + q * RA), u[q]);
+    }
   }
   pdl_launch_dependents();  // our items are done: the next kernel may launch
-}
-
-// ---------------------------------------------------------------------------
-// both passes in one persistent launch (N1 = N2 = M)
-// ---------------------------------------------------------------------------
-//
-// A unit is one selected template: n_det x NCB pass-1 items (P1) and n_det x
-// NRB pass-2 items (P2).  Each SM takes one role for the launch, P1 or P2
-// (the first CTA on an SM draws it from an alternating counter, the others on
-// that SM follow), so an SM runs one of the two large transform bodies and its
-// instruction cache holds it.  Each role claims its items in unit order from
-// its own queue; a producer whose queue is exhausted helps with the other.
-// Unit u writes its series to ring position u % ring of the scratch, so the
-// intermediate of the few units in flight stays in L2.  P2(u) waits until every
-// P1(u) item has completed and P1(u) until every P2(u - ring) item has its rows
-// in shared memory.  In the order P1(0) < P2(0) < P1(1) < ... every wait points
-// to an earlier item, both roles are present once CTAs run on two SMs, and a
-// producer signals its own completed items before it blocks, so the earliest
-// unfinished item always progresses.  All waits are bounded.
-
-constexpr int kFzEnd = 3;       // header kind: no more items
-constexpr int kFzMaxSm = 1024;  // per-SM role slots in the counter block
-
-struct FusedQ {
-  unsigned* queue;    // [2]: next P1 item, next P2 item
-  unsigned* roles;    // [1 + kFzMaxSm]: role counter, then per SM 0 = unassigned, 1 + role, or 3 = being set
-  unsigned* p1_done;  // per unit: completed P1 items
-  unsigned* p2_read;  // per unit: P2 items whose rows have landed
-  int n_units;
-  int ring;           // units of scratch (>= 2)
-};
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// spin until *p >= target or ~2^31 cycles pass (then record kStatusTimeout)
-__device__ __forceinline__ bool wait_count(const unsigned* p, uint32_t target, int* status) {
-  if (ld_acquire_u32(p) >= target) return true;
-  const long long t0 = clock64();
-  while (ld_acquire_u32(p) < target) {
-    __nanosleep(128);
-    if (clock64() - t0 > (1LL << 31)) {
-      atomicExch(status, kStatusTimeout);
-      return false;
-    }
-  }
-  return true;
-}
-
-template <int M, int BT, int QT>
-struct FusedGeo {
-  using PC = ColGeo<M, BT, QT>;
-  using PR = RowGeo<M>;
-  // 128-byte aligned slots: tensor-map copies land at their bases
-  static constexpr int SLOT = round128(PC::SLOT > PR::SLOT ? PC::SLOT : PR::SLOT);
-  static constexpr int TW_BYTES = PC::TW_BYTES;  // one sub-FFT table serves both passes
-  static constexpr int TW_OFF = 2 * SLOT;
-  static constexpr int BAR_OFF = TW_OFF + round128(TW_BYTES);
-  static constexpr int HDR_OFF = BAR_OFF + 64;  // per slot: int4 {kind, unit, loc, 0}
-  static constexpr int SMEM = HDR_OFF + 32;
-};
-
-template <int M, int BT, int QT>
-__global__ void __launch_bounds__(kColThreads, 3)
-    k_fused(const __grid_constant__ CUtensorMap tm, FilterArgs a, FusedQ f) {
-  constexpr int N1 = M, N2 = M;
-  using PC = ColGeo<M, BT, QT>;
-  using PR = RowGeo<M>;
-  using F = FusedGeo<M, BT, QT>;
-  using SG = ScratchGeo<M, M>;
-  constexpr int T = SubFft<M>::T, C = PC::C, R = PC::R, S = PC::S;
-  constexpr int NCB = N2 / C, RW = PR::RW, NRB = N1 / RW, PH = SG::P;
-  constexpr int64_t N = (int64_t)N1 * N2;
-  extern __shared__ __align__(128) unsigned char sm[];
-  const float2* tw = reinterpret_cast<const float2*>(sm + F::TW_OFF);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + F::BAR_OFF);  // [0], [1]: the slot's item is staged
-  uint64_t* empty = full + 2;                                     // [0], [1]: every compute warp done with it
-  uint64_t* twb = full + 4;                                       // the twiddle table landed
-  uint64_t* cbar = full + 5;                                      // barrier of the compute warps
-  int4* hdr = reinterpret_cast<int4*>(sm + F::HDR_OFF);
-  const int tid = threadIdx.x;
-  const uint32_t A = (uint32_t)(a.n_det * NCB), B = (uint32_t)(a.n_det * NRB);
-  const uint32_t total = (uint32_t)f.n_units * (A + B);  // items of both kinds
-  if (tid == 0) {
-    mbar_init(full + 0, 1);
-    mbar_init(full + 1, 1);
-    mbar_init(empty + 0, kColConsumers / 32);
-    mbar_init(empty + 1, kColConsumers / 32);
-    mbar_init(twb, 1);
-    mbar_init(cbar, kColConsumers / 32);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid >= kColConsumers) {
-    // copy-issuing warp: one lane claims items, waits for their dependencies and stages them.
-    // After any timed-out wait it claims nothing more: it lets the copies it issued land and
-    // returns (the status word reports the failure, the launch's results are void).
-    if (tid == kColConsumers) {
-      const unsigned char* qbase = static_cast<const unsigned char*>(QT == kBankF32 ? (const void*)a.q : a.q_lp);
-      const uint64_t pol_first = policy_evict_first();
-      mbar_expect_tx(twb, (uint32_t)F::TW_BYTES);
-      bulk_g2s(sm + F::TW_OFF, a.tw1, (uint32_t)F::TW_BYTES, twb);
-      pdl_wait();  // the weighted data come from the kernel just before
-      fence_proxy_async_global_fwd();
-      bool failed = false;
-      // P1 items whose completion is not yet signalled: unit and queue index (k) per slot.  A P1
-      // item is signalled once its slot is released; before blocking on a dependency the producer
-      // signals all of its own, so a blocked producer never holds an unsignalled item.
-      int pend_unit[2] = {-1, -1};
-      uint32_t pend_k[2] = {0, 0};
-      auto settle = [&](int sl) {
-        if (pend_unit[sl] < 0) return;
-        if (!failed && mbar_wait_bounded(empty + sl, (pend_k[sl] >> 1) & 1, a.status)) {
-          __threadfence();  // the compute warps' scratch stores -> visible to other CTAs
-          atomicAdd(f.p1_done + pend_unit[sl], 1u);
-        } else {
-          failed = true;
-        }
-        pend_unit[sl] = -1;
-      };
-      auto depend = [&](const unsigned* ctr, uint32_t target) {
-        if (ld_acquire_u32(ctr) >= target) return;
-        settle(0);
-        settle(1);
-        if (!failed && !wait_count(ctr, target, a.status)) failed = true;
-      };
-      // this SM's role: the first CTA here draws it, the others read it
-      uint32_t smid;
-      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-      unsigned* my = f.roles + 1 + (smid % kFzMaxSm);
-      int q = 0;  // queue: 0 = P1, 1 = P2
-      const unsigned prev = atomicCAS(my, 0u, 3u);
-      if (prev == 0) {
-        q = (int)(atomicAdd(f.roles, 1u) & 1u);
-        atomicExch(my, 1u + (unsigned)q);
-      } else {
-        unsigned v = prev;
-        const long long t0 = clock64();
-        while (v == 3u && clock64() - t0 < (1LL << 31)) v = ld_acquire_u32(my);
-        q = v == 2u ? 1 : 0;
-      }
-      bool switched = false;
-      // the next item is claimed, and its dependency met, while the compute warps work on the
-      // staged ones: when a slot is released its copies are issued at once
-      int kind = 0, unit = 0;
-      uint32_t loc = 0;
-      auto claim = [&]() {
-        for (;;) {
-          const uint32_t per = q == 0 ? A : B;
-          const uint32_t g = atomicAdd(f.queue + q, 1u);
-          if (g < (uint32_t)f.n_units * per) {
-            kind = q + 1;
-            unit = (int)(g / per);
-            loc = g % per;
-            break;
-          }
-          if (switched) {
-            kind = kFzEnd;
-            return;
-          }
-          switched = true;  // this role's items are all claimed: help with the other's
-          q ^= 1;
-        }
-        if (kind == 1 && unit >= f.ring) depend(f.p2_read + (unit - f.ring), B);
-        if (kind == 2) depend(f.p1_done + unit, A);
-      };
-      claim();
-      uint32_t k = 0;  // items staged
-      for (;; ++k) {
-        const int slot = k & 1;
-        if (k >= 2) {
-          settle(slot);
-          if (!failed && !mbar_wait_bounded(empty + slot, (uint32_t)(((k >> 1) + 1) & 1), a.status)) failed = true;
-        }
-        if (failed) break;
-        if (kind == kFzEnd) {
-          hdr[slot] = make_int4(kFzEnd, 0, 0, 0);
-          mbar_arrive(full + slot);
-          break;
-        }
-        unsigned char* dst = sm + slot * F::SLOT;
-        fence_proxy_async();
-        if (kind == 1) {
-          const int d = (int)(loc % (uint32_t)a.n_det), cb = (int)(loc / (uint32_t)a.n_det);
-          const int64_t tmpl = a.sel[a.pos0 + unit];
-          hdr[slot] = make_int4(1, unit, (int)loc, 0);
-          mbar_expect_tx(full + slot, (uint32_t)(C * (PC::H_COL + PC::Q_COL)));
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const int64_t col = (int64_t)cb * C + c;
-            bulk_g2s(dst + c * S * 8, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + col * R) * PC::HB,
-                     (uint32_t)PC::H_COL, full + slot);
-            bulk_g2s(dst + c * S * 8 + PC::H_COL, qbase + ((int64_t)d * a.ld_q + col * R) * PC::QB,
-                     (uint32_t)PC::Q_COL, full + slot);
-          }
-          pend_unit[slot] = unit;
-          pend_k[slot] = k;
-        } else {
-          fence_proxy_async_global_fwd();  // other CTAs' generic stores -> our async-proxy reads
-          const int d = (int)(loc / (uint32_t)NRB), j10 = (int)(loc % (uint32_t)NRB) * RW;
-          const int rs = (unit % f.ring) * a.n_det + d;  // ring series
-          hdr[slot] = make_int4(2, unit, (int)loc, 0);
-          mbar_expect_tx(full + slot, (uint32_t)(PR::ITEM * 8));
-          if constexpr (RW == PH) {
-            bulk_g2s_hint(dst, a.scratch + (int64_t)rs * N + (int64_t)j10 * N2, (uint32_t)(PR::ITEM * 8), full + slot,
-                          pol_first);
-          } else {
-            const int z = rs * (N1 / PH) + j10 / PH;
-#pragma unroll
-            for (int y = 0; y < N2; y += SG::BOXY)
-              tma_load_3d_hint(dst + (size_t)y * RW * 8, &tm, j10 % PH, y, z, full + slot, pol_first);
-          }
-        }
-        claim();
-      }
-      // the last staged items: after a failure, let their copies land (no end marker was staged,
-      // so each slot's last completed "full" phase is its last item's); signal their P1
-      // completions once the compute warps are done with them; then the next kernel may launch
-      if (failed)
-        for (uint32_t m = (k >= 2 ? k - 2 : 0); m < k; ++m) mbar_wait_bounded(full + (m & 1), (m >> 1) & 1, a.status);
-      settle(0);
-      settle(1);
-      for (uint32_t m = (k >= 2 ? k - 2 : 0); !failed && m < k; ++m)
-        if (!mbar_wait_bounded(empty + (m & 1), (uint32_t)((m >> 1) & 1), a.status)) failed = true;
-      pdl_launch_dependents();
-    }
-    return;
-  }
-  // compute warps.  Every wait is bounded; after a timed-out one the thread leaves the loop (the
-  // other compute warps then time out at their next barrier or slot and leave too).
-  const int ca = tid / T, ta = tid % T;
-  pdl_wait();  // the previous kernel (a reader of the scratch) has completed
-  if (!mbar_wait_bounded(twb, 0, a.status)) return;
-  RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, a.q_type == kBankF32 ? nullptr : a.dscale, a.pos0, a.n_det, a.window,
-            a.valid_begin, a.valid_end, a.n_win, a.n_sel_total, a.slots, a.row_valid};
-  uint32_t cuse = 0;  // completed uses of cbar
-  bool ok = true;
-  // barrier of the compute warps on an mbarrier (one arrival per warp, bounded wait)
-  auto compute_sync = [&]() {
-    __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(cbar);
-    ok = ok && mbar_wait_bounded(cbar, cuse & 1, a.status);
-    ++cuse;
-    return !ok;
-  };
-  // at most one item per queue position plus the end marker: the loop is bounded
-  for (uint32_t k = 0; k <= total && ok; ++k) {
-    const int slot = k & 1;
-    if (!mbar_wait_bounded(full + slot, (uint32_t)((k >> 1) & 1), a.status)) break;
-    const int4 h = hdr[slot];
-    if (h.x == kFzEnd) break;
-    unsigned char* sp = sm + slot * F::SLOT;
-    if (h.x == 1) {
-      const int unit = h.y, d = h.z % a.n_det, cb = h.z / a.n_det;
-      cols_column<N1, N2, BT, QT>(sp + ca * S * 8, tw, a.tw4, a.scratch + (int64_t)((unit % f.ring) * a.n_det + d) * N,
-                                  cb * C + ca, ta);
-    } else if (h.x == 2) {
-      const int unit = h.y, d = h.z / NRB, j10 = (h.z % NRB) * RW;
-      if (tid == 0) atomicAdd(f.p2_read + unit, 1u);  // the rows are in shared memory: the ring slot may be rewritten
-      if (!rows_item<N1, N2>(sp, tw, ep, unit * a.n_det + d, j10, tid, compute_sync, [&]() { compute_sync(); }))
-        break;
-      if (!ok) break;
-    }
-    // this warp is done with the slot: order its shared accesses before the next copies into it
-    fence_proxy_async();
-    __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(empty + slot);
-  }
-  pdl_launch_dependents();
 }
 
 template <class K>
@@ -792,40 +488,6 @@ cudaError_t run_rows(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st
   return e;
 }
 
-template <int M, int BT, int QT>
-cudaError_t run_fused(const FilterArgs& a, const CUtensorMap& tm, const FusedQ& q, cudaStream_t st) {
-  using F = FusedGeo<M, BT, QT>;
-  static_assert(F::SMEM * 3 <= 230400, "k_fused: three CTAs per SM must fit in shared memory");
-  auto k = k_fused<M, BT, QT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = set_smem2(k, F::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int64_t items = (int64_t)q.n_units * a.n_det * (M / ColGeo<M, BT, QT>::C + M / RowGeo<M>::RW);
-  cudaError_t e = launch_pdl(k, (int)std::min<int64_t>(items, (int64_t)sm_count() * 3), kColThreads, F::SMEM, st, tm, a, q);
-  add_launches(1);
-  return e;
-}
-
-template <int M>
-cudaError_t run_fused_bt(const FilterArgs& a, const CUtensorMap& tm, const FusedQ& q, cudaStream_t st) {
-  if (a.q_type == kBankF32) {
-    switch (a.bank_type) {
-      case kBankF32: return run_fused<M, kBankF32, kBankF32>(a, tm, q, st);
-      case kBankF16: return run_fused<M, kBankF16, kBankF32>(a, tm, q, st);
-      case kBankBF16: return run_fused<M, kBankBF16, kBankF32>(a, tm, q, st);
-    }
-  } else if (a.q_type == a.bank_type) {
-    switch (a.bank_type) {
-      case kBankF16: return run_fused<M, kBankF16, kBankF16>(a, tm, q, st);
-      case kBankBF16: return run_fused<M, kBankBF16, kBankBF16>(a, tm, q, st);
-    }
-  }
-  return cudaErrorInvalidValue;
-}
-
 // signature of the driver's cuTensorMapEncodeTiled (CUDA 12.0 ABI), fetched at run time
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -910,21 +572,6 @@ cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISP
 
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
   MF_DISPATCH2(a.n, run_rows, (a, tm, st))
-}
-
-bool fused_supported(int64_t n) { return n == (1 << 18) || n == (1 << 20); }
-
-int64_t fused_counter_words(int64_t n_units) { return 3 + kFzMaxSm + 2 * n_units; }
-
-cudaError_t launch_filter_fused(const FilterArgs& a, const CUtensorMap& tm, unsigned* counters, int n_units, int ring,
-                                cudaStream_t st) {
-  if (ring < 2 || n_units < 1) return cudaErrorInvalidValue;
-  FusedQ q{counters, counters + 2, counters + 3 + kFzMaxSm, counters + 3 + kFzMaxSm + n_units, n_units, ring};
-  switch (a.n) {
-    case 1 << 18: return run_fused_bt<512>(a, tm, q, st);
-    case 1 << 20: return run_fused_bt<1024>(a, tm, q, st);
-  }
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m) {

@@ -85,16 +85,6 @@ bool plan_capturable(const ::mf_plan_s* p);
 // half (k1 < N1/2) at k2 N1/2 + k1 (see launch_to_cols).
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& scratch_map, cudaStream_t st);
-// Both passes of the whole selection (a.pos0 .. a.pos0 + n_units templates) in
-// one persistent launch (N = 2^18 or 2^20): the scratch is used as a ring of
-// `ring` units of n_det series (2 <= ring <= scratch capacity in templates).
-// counters: fused_counter_words(n_units) words, zero at launch (work queues,
-// SM roles, pass-1 completions and pass-2 landings per unit).
-bool fused_supported(int64_t n);
-int64_t fused_counter_words(int64_t n_units);
-constexpr int64_t kFusedRingBytes = int64_t(64) << 20;  // intermediate ring, about half the L2
-cudaError_t launch_filter_fused(const FilterArgs& a, const CUtensorMap& scratch_map, unsigned* counters, int n_units,
-                                int ring, cudaStream_t st);
 // Tensor map of the pass-1 -> pass-2 scratch (`series` series of length n)
 // through which pass 2 reads its items; all zero where pass 2 needs none.
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m);

@@ -47,8 +47,7 @@ class mf_coinc(C.Structure):
 class mf_plan_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pass1_launches", C.c_int64), ("pass1_series", C.c_int64),
                 ("pass1_ms", C.c_double), ("pass2_launches", C.c_int64), ("pass2_series", C.c_int64),
-                ("pass2_ms", C.c_double), ("fused_launches", C.c_int64), ("fused_series", C.c_int64),
-                ("fused_ms", C.c_double), ("impl", C.c_int32), ("batch", C.c_int32)]
+                ("pass2_ms", C.c_double), ("impl", C.c_int32), ("batch", C.c_int32)]
 
 
 class mf_batch_desc(C.Structure):
@@ -63,7 +62,6 @@ class mf_batch_trigger(C.Structure):
 
 
 MF_RUN_SERIAL, MF_RUN_STREAMS, MF_RUN_GRAPH = 0, 1, 2
-MF_FILTER_TWO_PASS, MF_FILTER_FUSED = 0, 1
 BATCH_TRIGGER_NP = np.dtype([("det", np.int32), ("cls", np.int32), ("tmpl", np.int32), ("reserved", np.int32),
                              ("sample", np.int64), ("snr", np.float32), ("phase", np.float32)])
 
@@ -106,7 +104,6 @@ SIGNATURES = {
     "mf_batch_run": (C.c_int, [_P, _P, _I64, C.c_int32]),
     "mf_batch_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
     "mf_set_batch": (C.c_int, [_P, C.c_int32]),
-    "mf_set_filter_mode": (C.c_int, [_P, C.c_int32]),
     "mf_strain_to_fd": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_decimate": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_filter": (C.c_int, [_P, _P, _I64, _P, _I64]),
@@ -264,10 +261,6 @@ class Plan:
 
     def set_batch(self, batch):
         _check(self.h, self.lib.mf_set_batch(self.h, batch))
-
-    def set_filter_mode(self, mode):
-        """MF_FILTER_FUSED (default) or MF_FILTER_TWO_PASS (see mf_set_filter_mode)."""
-        _check(self.h, self.lib.mf_set_filter_mode(self.h, int(mode)))
 
     def sigmasq(self, n=None):
         n = self.n_tmpl if n is None else n
