@@ -203,6 +203,66 @@ def psd_welch(strain, fs, seg_len, stride, average="median"):
 
 
 # ---------------------------------------------------------------------------
+# gating of loud short transients before the filter (Sec. VI; the paper cites
+# the method without its statistic or parameters, so these are readings)
+# ---------------------------------------------------------------------------
+
+def gate_statistic(stilde, psd, n, fs, f_low, f_high):
+    """rho_g[d, j] = |z_g[j]| / sigma_g, the envelope of the band-limited
+    whitened strain in matched-filter SNR units:
+        z_g[j] = 4 df sum_{k in band} s~[k] / sqrt(S_n[k]) e^{+2 pi i j k / N},
+        sigma_g^2 = 4 df n_band
+    (the band of Eq. 2).  In Gaussian noise rho_g^2 has mean 2 (two
+    quadratures of unit variance)."""
+    s = np.atleast_2d(np.asarray(stilde, dtype=np.complex128))
+    m = band_mask(n, fs, f_low, f_high, psd)
+    df = fs / n
+    x = np.zeros((s.shape[0], n), dtype=np.complex128)
+    x[:, :n // 2 + 1][:, m] = s[:, m] / np.sqrt(np.asarray(psd, dtype=np.float64)[m])
+    z = 4.0 * df * n * np.fft.ifft(x, axis=-1)  # sum_k x[k] e^{+2 pi i j k / N}
+    return np.abs(z) / math.sqrt(4.0 * df * int(m.sum()))
+
+
+def gate_find(rho_g, thr, window, valid_begin=0, valid_end=None):
+    """Gates: per row, the peak sample of every window of `window` samples
+    that holds samples with rho_g >= thr (the filter's clustering rule,
+    cluster_windows).  Returns a TRIGGER_DTYPE array (tmpl 0, phase 0)
+    ordered by (det, sample)."""
+    rows = []
+    for d, r in enumerate(np.atleast_2d(rho_g)):
+        _, j, r2 = cluster_windows(np.asarray(r, dtype=np.float64) ** 2, thr, window, valid_begin, valid_end)
+        for jj, rr in zip(j, r2):
+            rows.append((d, 0, int(jj), math.sqrt(rr), 0.0))
+    return np.array(rows, dtype=TRIGGER_DTYPE)
+
+
+def gate_window(n, fs, centers, t_zero, t_taper):
+    """g[j] = product over gate centers c of the inverse Tukey window
+    W(|j - c| / fs): W(t) = 0 for t <= t_zero, (1 - cos(pi (t - t_zero) /
+    t_taper)) / 2 for t_zero < t < t_zero + t_taper, 1 beyond."""
+    j = np.arange(n, dtype=np.float64)
+    g = np.ones(n)
+    for c in centers:
+        t = np.abs(j - float(c)) / fs
+        w = np.ones(n)
+        w[t <= t_zero] = 0.0
+        m = (t > t_zero) & (t < t_zero + t_taper)
+        w[m] = 0.5 * (1.0 - np.cos(math.pi * (t[m] - t_zero) / t_taper))
+        g *= w
+    return g
+
+
+def gate_apply(strain, fs, gates, t_zero, t_taper):
+    """Gated strain: each row times gate_window of that row's gates."""
+    x = np.array(np.atleast_2d(strain), dtype=np.float64)
+    for d in range(x.shape[0]):
+        c = gates["sample"][gates["det"] == d]
+        if len(c):
+            x[d] *= gate_window(x.shape[1], fs, c, t_zero, t_taper)
+    return x
+
+
+# ---------------------------------------------------------------------------
 # signal-based veto at trigger times: chi^2_r and the re-weighted SNR (Eq. 4)
 # ---------------------------------------------------------------------------
 
