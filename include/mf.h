@@ -103,6 +103,34 @@ mf_status mf_set_psd(mf_plan_t plan, const double* psd, int64_t nbins);
 mf_status mf_psd_welch(double fs, int32_t n_det, int64_t n_samples, const float* strain, int64_t ld, int64_t seg_len,
                        int64_t stride, int32_t average, double* psd, void* cuda_stream);
 
+/* Gating of loud short transients before the filter (Sec. VI: short-duration
+ * artifacts are removed by gating before matched filtering; the paper cites
+ * the method without its statistic or parameters, so these are readings).
+ *
+ * mf_load_gate_template replaces the plan's bank by one row,
+ * h~[k] = sqrt(S_n[k]) on the band of Eq. (2) and 0 elsewhere, so that
+ * mf_filter computes the gate statistic
+ *   rho_g(t) = |z_g(t)| / sigma_g,
+ *   z_g(t) = 4 df sum_{k in band} s~[k] / sqrt(S_n[k]) e^{+2 pi i t k / N},
+ *   sigma_g^2 = 4 df n_band,
+ * the envelope of the band-limited whitened strain in matched-filter SNR units
+ * (rho_g^2 is chi^2 with 2 dof in Gaussian noise); the plan's triggers (per
+ * window, the peak with rho_g >= the plan's threshold, tmpl 0) are the gates.
+ * Needs the PSD (mf_set_psd).  Errors: MF_ESTATE, MF_ENOMEM, MF_ECUDA. */
+mf_status mf_load_gate_template(mf_plan_t plan);
+
+/* out[d][j] = strain[d][j] prod over the gates c of row d of W(|j - c| / fs),
+ * W(t) = 0 for t <= t_zero, (1 - cos(pi (t - t_zero) / t_taper)) / 2 for
+ * t_zero < t < t_zero + t_taper, 1 beyond (an inverse Tukey window; FP64).
+ * gates: device mf_trigger list sorted by (det, sample), the first
+ * min(*count, max_gates) used (mf_device_triggers of a plan loaded with
+ * mf_load_gate_template); count: device int64.  strain, out: device float32
+ * [n_det][ld], [n_det][ld_out] (out may be strain).  Asynchronous on
+ * cuda_stream.  Errors: MF_EINVAL, MF_ECUDA. */
+mf_status mf_gate_apply(const float* strain, int64_t ld, int32_t n_det, int64_t n, double fs, const mf_trigger* gates,
+                        const int64_t* count, int64_t max_gates, double t_zero, double t_taper, float* out,
+                        int64_t ld_out, void* cuda_stream);
+
 /* Replace the template bank (Sec. II; Table I): n_tmpl one-sided templates
  * h~_t[k], row t at htilde + t*ld elements, k = 0..N/2 (ld >= N/2+1).  dtype
  * MF_F32 (scales must be NULL) or MF_F16 / MF_BF16 with host float32

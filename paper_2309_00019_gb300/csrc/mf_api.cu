@@ -511,6 +511,24 @@ mf_status mf_set_batch(mf_plan_t p, int32_t batch) {
   return MF_OK;
 }
 
+mf_status mf_load_gate_template(mf_plan_t p) {
+  if (!p) return fail(p, MF_EINVAL, "mf_load_gate_template: null plan");
+  if (!p->psd_set) return fail(p, MF_ESTATE, "mf_load_gate_template: PSD not set");
+  mf_status s = mf_bank_reserve(p, MF_F32, 1);
+  if (s != MF_OK) return s;
+  float2* row = nullptr;
+  s = dalloc(p, &row, (size_t)p->nb * sizeof(float2), "gate row");
+  if (s != MF_OK) return s;
+  cudaError_t e = mf::launch_gate_row(p->w_dev, p->nb, p->d.fs / (double)p->d.n, row, p->st);
+  if (e != cudaSuccess) {
+    cudaFree(row);
+    return cuda_fail(p, e, "mf_load_gate_template");
+  }
+  s = mf_bank_set_rows(p, 0, 1, row, p->nb, nullptr, 1);  // synchronises before returning
+  cudaFree(row);
+  return s;
+}
+
 mf_status mf_load_bank(mf_plan_t p, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld, const float* scales,
                        int on_device) {
   if (!p || !htilde) return fail(p, MF_EINVAL, "mf_load_bank: null argument");

@@ -150,6 +150,9 @@ cudaError_t launch_compact(const unsigned long long* slots, int n_det, int64_t n
                            int64_t* count, int64_t* block_counts, int64_t n_blocks_cap, cudaStream_t st);
 int64_t compact_blocks(int64_t n_slots);
 // time series -> one-sided dt-normalised spectrum (A1)
+// Gate statistic's one-row bank (mf_gate.cu): row[k] = sqrt(4 df / w[k]) where
+// w[k] > 0 (the PSD weights of Eq. 2), else 0; k < nb, complex64.
+cudaError_t launch_gate_row(const double* w, int64_t nb, double df, float2* row, cudaStream_t st);
 cudaError_t launch_rfft(const float* strain, int64_t ld_s, int n_det, int64_t n, int n1, int n2, double dt,
                         float2* scratch, float2* dtilde, int64_t ld_d, cudaStream_t st);
 // keep bins 0..nb_out-1 (A2)

@@ -109,6 +109,9 @@ SIGNATURES = {
     "mf_filter": (C.c_int, [_P, _P, _I64, _P, _I64]),
     "mf_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
     "mf_device_triggers": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
+    "mf_load_gate_template": (C.c_int, [_P]),
+    "mf_gate_apply": (C.c_int, [_P, _I64, C.c_int32, _I64, C.c_double, _P, _P, _I64, C.c_double, C.c_double, _P,
+                                _I64, _P]),
     "mf_coincide": (C.c_int, [_P, C.POINTER(mf_coinc_desc), _P]),
     "mf_get_coincs": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
     "mf_set_nbhd": (C.c_int, [_P, _P, _P, _I64, C.c_int]),
@@ -296,6 +299,10 @@ class Plan:
         st = self.lib.mf_get_triggers(self.h, out.ctypes.data if cap else None, cap, C.byref(n))
         _check(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
         return out[: min(cap, n.value, self.desc.max_triggers)], n.value, st
+
+    def load_gate_template(self):
+        """One-row bank sqrt(S_n) on the band: filter() then finds the gates (mf_load_gate_template)."""
+        _check(self.h, self.lib.mf_load_gate_template(self.h))
 
     def device_triggers(self):
         t, c = _P(), _P()
@@ -498,6 +505,25 @@ def psd_welch(strain, fs, seg_len, stride, average="median", out=None, stream=No
         out = torch.zeros((n_det, seg_len // 2 + 1), dtype=torch.float64, device=strain.device)
     _check(None, load().mf_psd_welch(float(fs), n_det, n_samples, _ptr(strain), ld, seg_len, stride,
                                      0 if average == "mean" else 1, _ptr(out), stream))
+    return out
+
+
+def gate_apply(strain, gate_plan, t_zero, t_taper, out=None, stream=None):
+    """mf_gate_apply: device float32 strain [n_det, n] times the inverse Tukey windows of the
+    gates found by gate_plan's last filter (a plan loaded with load_gate_template); returns out."""
+    import torch
+
+    n_det, n = strain.shape
+    ld = strain.stride(0) if n_det > 1 else n
+    if strain.stride(1) != 1:
+        raise ValueError("gate_apply: rows must be contiguous")
+    if out is None:
+        out = torch.empty_like(strain)
+    ld_out = out.stride(0) if n_det > 1 else n
+    t, c = gate_plan.device_triggers()
+    _check(None, load().mf_gate_apply(_ptr(strain), ld, n_det, n, float(gate_plan.desc.fs), t, c,
+                                      gate_plan.desc.max_triggers, float(t_zero), float(t_taper), _ptr(out), ld_out,
+                                      stream))
     return out
 
 
