@@ -108,12 +108,14 @@ class Hierarchy:
 
     def run_host(self, strain_host):
         """End to end from host strain (pinned for an asynchronous copy): H2D, the
-        whole hot path, and D2H of the stage-2 triggers and stage-1 coincidences."""
+        whole hot path, and D2H of the stage-2 triggers and stage-1 coincidences into
+        page-locked buffers of the plans (the returned arrays are overwritten by the
+        next call)."""
         with self.torch.cuda.stream(self.stream):
             self.strain.copy_(strain_host, non_blocking=True)
         self.run()
-        trig2, n2, _ = self.p2.triggers()
-        co, nco, _ = self.p1.coincs()
+        trig2, n2, _ = self.p2.triggers(pinned=True)  # page-locked readback, valid until the next step
+        co, nco, _ = self.p1.coincs(pinned=True)
         return trig2, co
 
     def td_seconds(self):

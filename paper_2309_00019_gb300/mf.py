@@ -290,12 +290,28 @@ class Plan:
         sp = _ptr(subset) if (subset is not None and n_subset > 0) else None
         _check(self.h, self.lib.mf_filter(self.h, _ptr(dtilde), ld, sp, n_subset))
 
-    def triggers(self, cap=None):
+    def _host_buffer(self, name, count, dtype, pinned):
+        """Host array of `count` records: a fresh one, or (pinned) a view of a page-locked buffer the
+        plan keeps and reuses (valid until the next call that uses it)."""
+        if not pinned:
+            return np.empty(count, dtype=dtype)
+        import torch
+
+        need = count * dtype.itemsize
+        buf = getattr(self, name, None)
+        if buf is None or buf.numel() < need:
+            buf = torch.empty(max(need, 1), dtype=torch.uint8, pin_memory=True)
+            setattr(self, name, buf)
+        return buf.numpy()[:need].view(dtype)
+
+    def triggers(self, cap=None, pinned=False):
+        """Triggers of the last filter (mf_get_triggers).  pinned: read into a page-locked buffer
+        of the plan (faster; the array is overwritten by the next pinned call)."""
         n = _I64(0)
         if cap is None:
             _check(self.h, self.lib.mf_get_triggers(self.h, None, 0, C.byref(n)), ok=(MF_OK, MF_EOVERFLOW))
             cap = n.value
-        out = np.zeros(cap, dtype=TRIGGER_NP)
+        out = self._host_buffer("_pinned_trig", cap, TRIGGER_NP, pinned)
         st = self.lib.mf_get_triggers(self.h, out.ctypes.data if cap else None, cap, C.byref(n))
         _check(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
         return out[: min(cap, n.value, self.desc.max_triggers)], n.value, st
@@ -317,12 +333,12 @@ class Plan:
         _check(self.h, self.lib.mf_coincide(self.h, C.byref(d), _ptr(followed)))
         self.coinc_cap = max(getattr(self, "coinc_cap", 0), max_coincs)
 
-    def coincs(self, cap=None):
+    def coincs(self, cap=None, pinned=False):
         n = _I64(0)
         if cap is None:
             _check(self.h, self.lib.mf_get_coincs(self.h, None, 0, C.byref(n)), ok=(MF_OK, MF_EOVERFLOW))
             cap = n.value
-        out = np.zeros(cap, dtype=COINC_NP)
+        out = self._host_buffer("_pinned_coinc", cap, COINC_NP, pinned)
         st = self.lib.mf_get_coincs(self.h, out.ctypes.data if cap else None, cap, C.byref(n))
         _check(self.h, st, ok=(MF_OK, MF_EOVERFLOW))
         return out[: min(cap, n.value, getattr(self, "coinc_cap", cap))], n.value, st

@@ -72,6 +72,9 @@ def test_end_to_end_from_host_strain(small_run):
     trig_dev, _, _ = h.p2.triggers()
     assert np.array_equal(trig2, trig_dev)
     assert len(co) > 0
+    # a second pinned read reuses the plan's page-locked buffer and gives the same records
+    again, _, _ = h.p2.triggers(pinned=True)
+    assert np.array_equal(again, trig_dev)
 
 
 def test_background_far_of_the_coincidences(small_run):
