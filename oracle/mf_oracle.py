@@ -310,6 +310,49 @@ def newsnr(rho, chi2_r):
 
 
 # ---------------------------------------------------------------------------
+# sine-Gaussian veto of heavy templates (Sec. III: triggers of templates above
+# 30 solar masses are further re-weighted with chi^2_sg; the paper cites the
+# test without its tiles or normalisation, so these are readings)
+# ---------------------------------------------------------------------------
+
+def sg_tile(n, fs, f0, q):
+    """One-sided spectrum of a sine-Gaussian tile of central frequency f0 and
+    quality factor q: g~[k] = exp(-(pi tau (f_k - f0))^2), tau = q / (sqrt(2) pi f0)
+    (the positive-frequency part of the transform of exp(-t^2 / tau^2) cos(2 pi f0 t),
+    up to a constant), k = 0..N/2."""
+    f = np.arange(n // 2 + 1) * (fs / n)
+    tau = q / (math.sqrt(2.0) * math.pi * f0)
+    return np.exp(-(math.pi * tau * (f - f0)) ** 2)
+
+
+def sg_chisq(stilde, w, n, fs, sample, f_final, offsets, q, f_high):
+    """Reduced sine-Gaussian chi^2 at one sample: tiles at f_l = f_final + offsets[l]
+    (those below f_high), each with SNR rho_l = |sum_k w s~ g~_l e^{+2 pi i k j / N}| / sigma_l,
+    sigma_l^2 = sum_k w g~_l^2, and chi2_r = sum_l rho_l^2 / (2 n_used) (mean 1 in Gaussian
+    noise).  Returns (chi2_r, n_used)."""
+    s = np.asarray(stilde, dtype=np.complex128)
+    k = np.arange(n // 2 + 1)
+    ph = np.exp(2j * math.pi * k * int(sample) / n)
+    tot, used = 0.0, 0
+    for off in offsets:
+        f0 = float(f_final) + float(off)
+        if f0 >= f_high:
+            continue
+        g = sg_tile(n, fs, f0, q)
+        z = np.sum(w * s * g * ph)
+        tot += abs(z) ** 2 / np.sum(w * g * g)
+        used += 1
+    return (tot / (2 * used) if used else 0.0), used
+
+
+def sg_newsnr(newsnr_value, chi2_r):
+    """rho^ = rho~ when chi2_r <= 4, else rho~ (chi2_r / 4)^(-1/2)."""
+    r = np.asarray(newsnr_value, dtype=np.float64)
+    c = np.asarray(chi2_r, dtype=np.float64)
+    return np.where(c > 4.0, r * np.sqrt(4.0 / np.maximum(c, 4.0)), r)
+
+
+# ---------------------------------------------------------------------------
 # overlapping segments of long data (Sec. V.C)
 # ---------------------------------------------------------------------------
 
