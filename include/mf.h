@@ -264,6 +264,27 @@ mf_status mf_get_stats(mf_plan_t plan, mf_plan_stats* out, int reset);
  * filter run), MF_ENOMEM. */
 mf_status mf_chisq(mf_plan_t plan, int32_t n_bands, float* chi2, float* newsnr);
 
+/* Sine-Gaussian veto of heavy templates at trigger times (Sec. III: triggers
+ * of templates heavier than 30 M_sun are further re-weighted with chi^2_sg
+ * against short glitches; the paper cites the test without its tiles or
+ * normalisation, this is the reading).  For trigger i of the device trigger
+ * list (template t, detector d, sample j) with mtotal[t] > m_min and
+ * snr_in[i] >= snr_min, tiles l = 0..n_tiles-1 at f_l = f_final[t] +
+ * offsets[l] (those at or above the band's upper edge skipped), spectra
+ * g~_l[k] = exp(-(pi tau_l (f_k - f_l))^2), tau_l = q / (sqrt(2) pi f_l), give
+ *   rho_l^2 = |sum_k w s~ g~_l e^{+2 pi i k j / N}|^2 / sum_k w g~_l^2
+ * (w = 4 df / S_n on the band, Eq. 2), and
+ *   chi2_r[i]  = sum_l rho_l^2 / (2 n_used)   (mean 1 in Gaussian noise),
+ *   snr_hat[i] = snr_in[i] if chi2_r <= 4, else snr_in[i] (chi2_r / 4)^{-1/2};
+ * other triggers get chi2_r 0 and snr_hat = snr_in.  f_final, mtotal: device
+ * float [n_tmpl] (Hz, solar masses); offsets: host double [n_tiles] (Hz),
+ * 1 <= n_tiles <= 16; snr_in (e.g. mf_chisq's newsnr), chi2_r, snr_hat:
+ * device float [max_triggers] in trigger order.  Asynchronous on the plan's
+ * stream.  Errors: MF_EINVAL, MF_ESTATE (no filter run), MF_ECUDA. */
+mf_status mf_sgchisq(mf_plan_t plan, const float* f_final, const float* mtotal, float m_min, float snr_min,
+                     int32_t n_tiles, const double* offsets, double q, const float* snr_in, float* chi2_r,
+                     float* snr_hat);
+
 /* Failure detection without a GPU fault (no counterpart in the paper): every
  * device wait in the filter kernels is bounded; on expiry it records a timeout
  * in the plan's status word, the kernel returns, and the next mf_get_triggers

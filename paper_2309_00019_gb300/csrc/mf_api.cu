@@ -740,6 +740,28 @@ mf_status mf_chisq(mf_plan_t p, int32_t n_bands, float* chi2, float* newsnr) {
   return MF_OK;
 }
 
+mf_status mf_sgchisq(mf_plan_t p, const float* f_final, const float* mtotal, float m_min, float snr_min,
+                     int32_t n_tiles, const double* offsets, double q, const float* newsnr, float* chi2_r,
+                     float* snr_hat) {
+  if (!p || !f_final || !mtotal || !offsets || !newsnr || !chi2_r || !snr_hat)
+    return fail(p, MF_EINVAL, "mf_sgchisq: null argument");
+  if (n_tiles < 1 || n_tiles > mf::kMaxSgTiles || !(q > 0)) return fail(p, MF_EINVAL, "mf_sgchisq: tiles or q");
+  if (!p->filtered) return fail(p, MF_ESTATE, "mf_sgchisq: no filter run");
+  mf::SgTiles tiles{};
+  tiles.n = n_tiles;
+  tiles.q = q;
+  for (int i = 0; i < n_tiles; ++i) tiles.offset[i] = offsets[i];
+  const bool lp = p->data_dtype != MF_F32;
+  // the band's upper edge: tiles at or above it are skipped
+  const double f_high = std::min(p->d.f_high, p->d.fs / 2.0);
+  cudaError_t e = mf::launch_sgchisq(p->trig, p->count, p->d.max_triggers, lp ? p->q_lp : (const void*)p->q,
+                                     bank_type(p->data_dtype), p->ld_q, p->n1, p->n2, p->w_dev, p->d.fs / (double)p->d.n,
+                                     f_high, f_final, mtotal, m_min, snr_min, tiles, p->sigma_ref,
+                                     lp ? p->dscale : nullptr, newsnr, chi2_r, snr_hat, p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mf_sgchisq");
+  return MF_OK;
+}
+
 mf_status mf_far(const float* stat_fg, int64_t n_fg, const float* stat_bg, int64_t n_bg, double t_bg, double scale,
                  double fit_min, double* far_count, double* far_fit, double* alpha, double* beta) {
   if (n_fg < 0 || n_bg < 0 || (n_fg > 0 && (!stat_fg || !far_count)) || (n_bg > 0 && !stat_bg))

@@ -281,4 +281,109 @@ cudaError_t launch_chisq(const void* trig, const int64_t* count, int64_t cap, co
   return cudaGetLastError();
 }
 
+namespace {
+
+// One CTA per trigger: for a trigger of a template heavier than m_min and with rho~ >= snr_min, the SNR of
+// every sine-Gaussian tile at the trigger sample.  Tile l of template t: f_l = f_final[t] + offsets[l]
+// (skipped at or above f_high), g~[k] = exp(-(pi tau (f_k - f_l))^2), tau = qf / (sqrt(2) pi f_l); only the
+// bins within 6 / (pi tau) of f_l enter (beyond, g~ < 3e-16).  rho_l^2 = |sum_k w s~ g~ e^{+2 pi i k j / N}|^2
+// / sum_k w g~^2 with the weighted data read in the column layout and rescaled from its stored units.
+template <int QT>
+__global__ void __launch_bounds__(kCT) k_sgchisq(const TrigRecC* __restrict__ trig, const int64_t* __restrict__ count,
+                                                 int64_t cap, const void* __restrict__ q, int64_t ld_q, int n1, int n2,
+                                                 const double* __restrict__ w, double df, double f_high,
+                                                 const float* __restrict__ f_final, const float* __restrict__ mtotal,
+                                                 float m_min, float snr_min, SgTiles tiles, double q_to_true,
+                                                 const float* __restrict__ dscale, const float* __restrict__ snr_in,
+                                                 float* __restrict__ chi2_r, float* __restrict__ snr_hat) {
+  __shared__ double red[3][kCT];
+  const int64_t n_trig = *count < cap ? *count : cap;
+  const int R = n1 / 2;
+  const int64_t nb = (int64_t)R * n2 + 1;  // bins 0 .. N/2
+  const uint64_t N = (uint64_t)n1 * (uint64_t)n2;
+  for (int64_t it = blockIdx.x; it < n_trig; it += gridDim.x) {
+    const TrigRecC tr = trig[it];
+    const float rho = snr_in[it];
+    if (!(mtotal[tr.tmpl] > m_min) || !(rho >= snr_min)) {
+      if (threadIdx.x == 0) {
+        chi2_r[it] = 0.f;
+        snr_hat[it] = rho;
+      }
+      continue;
+    }
+    const void* qrow = static_cast<const unsigned char*>(q) + (int64_t)tr.det * ld_q * (QT == kBankF32 ? 8 : 4);
+    const double scale = dscale ? q_to_true / (double)dscale[tr.det] : q_to_true;
+    const uint64_t j = (uint64_t)tr.sample;
+    double total = 0.0;
+    int used = 0;
+    for (int l = 0; l < tiles.n; ++l) {
+      const double f0 = (double)f_final[tr.tmpl] + tiles.offset[l];
+      if (!(f0 < f_high)) continue;
+      const double tau = tiles.q / (1.4142135623730951 * 3.141592653589793 * f0);
+      const double half = 6.0 / (3.141592653589793 * tau);
+      const int64_t klo = max((int64_t)1, (int64_t)ceil((f0 - half) / df));
+      const int64_t khi = min(nb - 2, (int64_t)floor((f0 + half) / df));
+      float ar = 0.f, ai = 0.f;
+      double s2 = 0.0;
+      for (int64_t k = klo + threadIdx.x; k <= khi; k += kCT) {
+        const double wk = w[k];
+        if (wk == 0.0) continue;
+        const float x = (float)(3.141592653589793 * tau * ((double)k * df - f0));
+        const float g = expf(-x * x);
+        const float2 qk = BankElem<QT>::get(qrow, (int64_t)(k % n2) * R + k / n2);  // column layout
+        float sn, cs;
+        sincospif(2.0f * (float)((k * j) % N) / (float)N, &sn, &cs);
+        ar += g * (qk.x * cs - qk.y * sn);
+        ai += g * (qk.x * sn + qk.y * cs);
+        s2 += wk * (double)g * (double)g;
+      }
+      red[0][threadIdx.x] = ar;
+      red[1][threadIdx.x] = ai;
+      red[2][threadIdx.x] = s2;
+      __syncthreads();
+      if (threadIdx.x == 0) {  // fixed-order sums
+        double zr = 0.0, zi = 0.0, ss = 0.0;
+        for (int i = 0; i < kCT; ++i) {
+          zr += red[0][i];
+          zi += red[1][i];
+          ss += red[2][i];
+        }
+        if (ss > 0.0) {
+          total += (zr * zr + zi * zi) * scale * scale / ss;
+          ++used;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double c = used ? total / (2.0 * used) : 0.0;
+      chi2_r[it] = (float)c;
+      snr_hat[it] = c > 4.0 ? (float)((double)rho * sqrt(4.0 / c)) : rho;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sgchisq(const void* trig, const int64_t* count, int64_t cap, const void* q, int q_type, int64_t ld_q,
+                           int n1, int n2, const double* w, double df, double f_high, const float* f_final,
+                           const float* mtotal, float m_min, float snr_min, const SgTiles& tiles, double q_to_true,
+                           const float* dscale, const float* snr_in, float* chi2_r, float* snr_hat, cudaStream_t st) {
+  if (tiles.n < 1 || tiles.n > kMaxSgTiles || !(tiles.q > 0)) return cudaErrorInvalidValue;
+  const int grid = sms_c() * 4;
+  const TrigRecC* t = static_cast<const TrigRecC*>(trig);
+#define MF_SG(QT)                                                                                                  \
+  k_sgchisq<QT><<<grid, kCT, 0, st>>>(t, count, cap, q, ld_q, n1, n2, w, df, f_high, f_final, mtotal, m_min, snr_min, \
+                                      tiles, q_to_true, dscale, snr_in, chi2_r, snr_hat)
+  switch (q_type) {
+    case kBankF32: MF_SG(kBankF32); break;
+    case kBankF16: MF_SG(kBankF16); break;
+    case kBankBF16: MF_SG(kBankBF16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef MF_SG
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace mf

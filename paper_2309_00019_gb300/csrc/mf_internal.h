@@ -110,6 +110,18 @@ cudaError_t launch_prep_cols(const float2* dtilde, int64_t ld_d, const double* w
 int64_t chisq_blocks(int n1, int n2);
 cudaError_t launch_chisq_edges(const void* bank, int bank_type, int64_t ld_bank, int64_t n_tmpl, int n1, int n2,
                                const double* w, int64_t nb, double* bpow, int p, int32_t* edges, cudaStream_t st);
+// Sine-Gaussian veto of heavy templates at trigger times (mf_chisq.cu): the tiles' offsets above each
+// template's final frequency (Hz) and their quality factor.
+constexpr int kMaxSgTiles = 16;
+struct SgTiles {
+  int n;
+  double q;
+  double offset[kMaxSgTiles];
+};
+cudaError_t launch_sgchisq(const void* trig, const int64_t* count, int64_t cap, const void* q, int q_type, int64_t ld_q,
+                           int n1, int n2, const double* w, double df, double f_high, const float* f_final,
+                           const float* mtotal, float m_min, float snr_min, const SgTiles& tiles, double q_to_true,
+                           const float* dscale, const float* snr_in, float* chi2_r, float* snr_hat, cudaStream_t st);
 cudaError_t launch_chisq(const void* trig, const int64_t* count, int64_t cap, const void* bank, int bank_type,
                          int64_t ld_bank, const void* q, int q_type, int64_t ld_q, int n1, int n2, const int32_t* edges,
                          int p, const float* ratio, const float* dscale, float* chi2, float* newsnr, cudaStream_t st);

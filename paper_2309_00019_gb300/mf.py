@@ -110,6 +110,7 @@ SIGNATURES = {
     "mf_get_triggers": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
     "mf_device_triggers": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
     "mf_load_gate_template": (C.c_int, [_P]),
+    "mf_sgchisq": (C.c_int, [_P, _P, _P, C.c_float, C.c_float, C.c_int32, _P, C.c_double, _P, _P, _P]),
     "mf_gate_apply": (C.c_int, [_P, _I64, C.c_int32, _I64, C.c_double, _P, _P, _I64, C.c_double, C.c_double, _P,
                                 _I64, _P]),
     "mf_coincide": (C.c_int, [_P, C.POINTER(mf_coinc_desc), _P]),
@@ -255,6 +256,15 @@ class Plan:
     def chisq(self, n_bands, chi2, newsnr):
         """chi^2 and the re-weighted SNR of the last filter's triggers into device float arrays."""
         _check(self.h, self.lib.mf_chisq(self.h, n_bands, _ptr(chi2), _ptr(newsnr)))
+
+    def sgchisq(self, f_final, mtotal, snr_in, chi2_r, snr_hat, m_min=30.0, snr_min=0.0,
+                offsets=(15.0, 30.0, 45.0, 60.0, 75.0, 90.0, 105.0, 120.0), q=20.0):
+        """Sine-Gaussian veto of the last filter's triggers (mf_sgchisq): f_final, mtotal device float
+        [n_tmpl]; snr_in, chi2_r, snr_hat device float [max_triggers]."""
+        off = np.ascontiguousarray(offsets, dtype=np.float64)
+        _check(self.h, self.lib.mf_sgchisq(self.h, _ptr(f_final), _ptr(mtotal), float(m_min), float(snr_min),
+                                           len(off), off.ctypes.data, float(q), _ptr(snr_in), _ptr(chi2_r),
+                                           _ptr(snr_hat)))
 
     def selftest_wait(self):
         """Run the bounded-wait self-test; returns the number of threads that came back."""
