@@ -64,10 +64,14 @@ __device__ __forceinline__ int64_t key_sample(unsigned long long key) {
 }
 __device__ __forceinline__ float key_rho2(unsigned long long key) { return __uint_as_float((uint32_t)(key >> 32)); }
 
+// One thread per detector-0 window maximum.  Sample positions are below 2^21, so the ring arithmetic is
+// 32-bit, and the ring position of shift k follows from shift k - 1 by one subtraction.
 __global__ void k_coinc(CoincArgs a) {
   const int64_t total = a.n_sel * a.n_win;
   const float need = fminf(a.rho_c_thr2, a.rho_c_store2);
-  const int64_t R = a.ring_end - a.ring_begin;
+  const int32_t R = (int32_t)(a.ring_end - a.ring_begin), rb = (int32_t)a.ring_begin;
+  const int32_t win = (int32_t)a.window, cw = (int32_t)a.coinc_window;
+  const int32_t step = (int32_t)(a.shift % (int64_t)R);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long kh = a.slots[i];  // detector 0, position p, window w
     if (kh == 0ull) continue;
@@ -77,27 +81,29 @@ __global__ void k_coinc(CoincArgs a) {
     const int64_t sh = key_sample(kh);
     const unsigned long long* row1 = a.slots + (a.n_sel + p) * a.n_win;
     const int32_t tmpl = a.sel[p];
-    const int64_t xh = sh - a.ring_begin;
+    int32_t x = (int32_t)(sh - a.ring_begin);  // ring position of the detector-0 sample, in [0, R)
     for (int k = 0; k <= a.n_shifts; ++k) {
       // detector-1 triggers at ring position x +- window land on s_h after a shift of k * shift
-      int64_t x = (xh - (int64_t)k * a.shift) % R;
-      if (x < 0) x += R;
-      int64_t lo[2], hi[2];
+      if (k > 0) {
+        x -= step;
+        if (x < 0) x += R;
+      }
+      int32_t lo[2], hi[2];
       int nint = 1;
-      lo[0] = x - a.coinc_window;
-      hi[0] = x + a.coinc_window;
+      lo[0] = x - cw;
+      hi[0] = x + cw;
       if (lo[0] < 0) {
         lo[1] = lo[0] + R; hi[1] = R - 1; lo[0] = 0; nint = 2;
       } else if (hi[0] >= R) {
         lo[1] = 0; hi[1] = hi[0] - R; hi[0] = R - 1; nint = 2;
       }
       for (int q = 0; q < nint; ++q) {
-        const int64_t w0 = (lo[q] + a.ring_begin) / a.window;
-        const int64_t w1 = (hi[q] + a.ring_begin) / a.window;
-        for (int64_t w = w0; w <= w1; ++w) {
+        const int32_t w0 = (lo[q] + rb) / win;
+        const int32_t w1 = (hi[q] + rb) / win;
+        for (int32_t w = w0; w <= w1; ++w) {
           const unsigned long long kl = row1[w];
           if (kl == 0ull) continue;
-          const int64_t y = key_sample(kl) - a.ring_begin;
+          const int32_t y = (int32_t)(key_sample(kl) - a.ring_begin);
           if (y < lo[q] || y > hi[q]) continue;
           const float r2l = key_rho2(kl);
           const float rc2 = r2h + r2l;
@@ -106,7 +112,7 @@ __global__ void k_coinc(CoincArgs a) {
             const unsigned long long slot = atomicAdd(a.n_coinc, 1ull);
             if ((int64_t)slot < a.coinc_cap) {
               CoincRec* out = reinterpret_cast<CoincRec*>(a.coincs);
-              out[slot] = CoincRec{tmpl, k, sh, y + a.ring_begin, sqrtf(r2h), sqrtf(r2l), sqrtf(rc2), 0};
+              out[slot] = CoincRec{tmpl, k, sh, (int64_t)y + a.ring_begin, sqrtf(r2h), sqrtf(r2l), sqrtf(rc2), 0};
             }
           }
         }
