@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "template-seconds filtered/s on 1 GB300 at SNR err<=1e-3; % HBM roofline"
 UNIT = "template-seconds/s"
+WORKLOAD = ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000 @ 512 Hz (N=2^18), "
+            "fine 20000 @ 2048 Hz (N=2^20) on the nbhd union")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -230,8 +232,8 @@ def reference_arm(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "two-stage hierarchical search, 2 det x 512 s @ 2048 Hz (oracle sample)",
-                   "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOAD if not args.small else "scaled-down 32 s hierarchy (check run)",
+                   "l2": "n/a (CPU)", "parallelism": "1 segment on the host cores (rank 0 only)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"per step: {desc}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -402,9 +404,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000 @ 512 Hz "
-                                    "(N=2^18), fine 20000 @ 2048 Hz (N=2^20) on the nbhd union"
-                                    if not args.small else "scaled-down 32 s hierarchy (check run)"),
+            "config": {"workload": WORKLOAD if not args.small else "scaled-down 32 s hierarchy (check run)",
                        "union_templates": int(statistics.mean(unions)),
                        "td_seconds_per_step": td_total / args.steps,
                        "l2": "512 MB buffer written between timed steps; banks (1 GB + 84 GB) streamed from HBM",
