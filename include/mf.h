@@ -274,8 +274,8 @@ mf_status mf_chisq(mf_plan_t plan, int32_t n_bands, float* chi2, float* newsnr);
  * g~_l[k] = exp(-(pi tau_l (f_k - f_l))^2), tau_l = q / (sqrt(2) pi f_l), give
  *   rho_l^2 = |sum_k w s~ g~_l e^{+2 pi i k j / N}|^2 / sum_k w g~_l^2
  * (w = 4 df / S_n on the band, Eq. 2), and
- *   chi2_r[i]  = sum_l rho_l^2 / (2 n_used)   (mean 1 in Gaussian noise),
- *   snr_hat[i] = snr_in[i] if chi2_r <= 4, else snr_in[i] (chi2_r / 4)^{-1/2};
+ *   chi2_r[i]  = sum_l rho_l^2 / (2 n_used)   (chi^2_sg, mean 1 in Gaussian noise),
+ *   snr_hat[i] = snr_in[i] chi2_r^{-1/2} if chi2_r >= 6, else snr_in[i]  (Eq. 3);
  * other triggers get chi2_r 0 and snr_hat = snr_in.  f_final, mtotal: device
  * float [n_tmpl] (Hz, solar masses); offsets: host double [n_tiles] (Hz),
  * 1 <= n_tiles <= 16; snr_in (e.g. mf_chisq's newsnr), chi2_r, snr_hat:

@@ -345,11 +345,12 @@ def sg_chisq(stilde, w, n, fs, sample, f_final, offsets, q, f_high):
     return (tot / (2 * used) if used else 0.0), used
 
 
-def sg_newsnr(newsnr_value, chi2_r):
-    """rho^ = rho~ when chi2_r <= 4, else rho~ (chi2_r / 4)^(-1/2)."""
+def sg_newsnr(newsnr_value, chi2_sg):
+    """Eq. (3): rho^ = rho~ (chi2_sg)^(-1/2) when chi2_sg >= 6 (inclusive), else rho~.
+    chi2_sg is the reduced statistic of sg_chisq (mean 1 in Gaussian noise)."""
     r = np.asarray(newsnr_value, dtype=np.float64)
-    c = np.asarray(chi2_r, dtype=np.float64)
-    return np.where(c > 4.0, r * np.sqrt(4.0 / np.maximum(c, 4.0)), r)
+    c = np.asarray(chi2_sg, dtype=np.float64)
+    return np.where(c >= 6.0, r / np.sqrt(np.maximum(c, 6.0)), r)
 
 
 # ---------------------------------------------------------------------------

@@ -356,9 +356,10 @@ __global__ void __launch_bounds__(kCT) k_sgchisq(const TrigRecC* __restrict__ tr
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      const double c = used ? total / (2.0 * used) : 0.0;
-      chi2_r[it] = (float)c;
-      snr_hat[it] = c > 4.0 ? (float)((double)rho * sqrt(4.0 / c)) : rho;
+      const float c = used ? (float)(total / (2.0 * used)) : 0.f;
+      chi2_r[it] = c;
+      // Eq. 3, inclusive at 6; decided on the stored single-precision value
+      snr_hat[it] = c >= 6.f ? (float)((double)rho / sqrt((double)c)) : rho;
     }
   }
 }

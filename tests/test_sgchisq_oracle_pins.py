@@ -1,7 +1,9 @@
 """Pins of the oracle's sine-Gaussian veto (CPU): the tile's spectrum against the
 discrete transform of its time-domain form, the reduced statistic's mean of 1 in
-Gaussian noise, a glitch in one tile that the veto cuts down, a chirp that it
-leaves alone, and the re-weighting rule's closed forms."""
+Gaussian noise (where the re-weighting of Eq. 3 leaves every trigger alone), a
+glitch in one tile that the veto cuts down, a chirp that it leaves alone, and the
+values Eq. (3) fixes: rho^ = rho~ (chi^2_sg)^(-1/2) from chi^2_sg = 6 on,
+inclusive, rho^ = rho~ below."""
 
 import math
 
@@ -41,6 +43,11 @@ def test_reduced_statistic_has_mean_one_in_gaussian_noise():
             vals.append(c)
     v = np.array(vals)
     assert abs(v.mean() - 1.0) < 0.12  # 300 correlated-tile draws; each rho_l^2 / 2 has mean 1
+    # on this scale Eq. (3)'s threshold of 6 is far in the noise tail, so Gaussian-noise triggers keep
+    # rho~; the unreduced sum (2 n_used times larger, mean 16) would cross it in most draws
+    assert v.max() < 6.0
+    assert np.array_equal(O.sg_newsnr(np.full(v.shape, 5.0), v), np.full(v.shape, 5.0))
+    assert np.mean(16.0 * v >= 6.0) > 0.9
 
 
 def test_glitch_in_a_tile_is_cut_and_a_chirp_is_not():
@@ -70,14 +77,21 @@ def test_glitch_in_a_tile_is_cut_and_a_chirp_is_not():
     r2, _ = O.snr_squared(s, h, w, n)
     j = int(np.argmax(r2))
     c, _ = O.sg_chisq(s, w, n, fs, j, f_final, OFFSETS, 20.0, fs / 2)
-    assert c < 4.0
+    assert c < 6.0
     assert O.sg_newsnr(math.sqrt(r2[j]), c) == pytest.approx(math.sqrt(r2[j]))
 
 
-def test_reweighting_rule_closed_forms_and_skipped_tiles():
-    assert O.sg_newsnr(10.0, 4.0) == 10.0
-    assert O.sg_newsnr(10.0, 16.0) == pytest.approx(5.0)
-    assert O.sg_newsnr(9.0, 36.0) == pytest.approx(3.0)
+def test_eq3_values_and_skipped_tiles():
+    # Eq. (3): rho^ = rho~ (chi^2_sg)^(-1/2) if chi^2_sg >= 6, rho~ otherwise
+    assert O.sg_newsnr(12.0, 9.0) == pytest.approx(4.0, rel=1e-15)  # chi^2_sg = 9: rho~ / 3
+    assert O.sg_newsnr(10.0, 6.0) == pytest.approx(10.0 / math.sqrt(6.0), rel=1e-15)  # inclusive at 6
+    below = np.nextafter(6.0, 0.0)
+    assert O.sg_newsnr(10.0, below) == 10.0  # just below 6: untouched (the printed rule jumps at 6)
+    for c in (0.0, 1.0, 4.0, 5.0, 5.999):
+        assert O.sg_newsnr(7.5, c) == 7.5
+    assert O.sg_newsnr(10.0, 100.0) == pytest.approx(1.0, rel=1e-15)
+    r = np.array([3.5, 8.0, 20.0])
+    assert np.allclose(O.sg_newsnr(r, np.array([6.25, 16.0, 400.0])), r / np.array([2.5, 4.0, 20.0]), rtol=1e-15)
     n, fs = 4096, 512.0
     w = O.weights(n, fs, 20.0, fs / 2, synth.psd_bins(n, fs))
     s = np.zeros(n // 2 + 1, dtype=np.complex128)
