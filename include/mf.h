@@ -489,11 +489,15 @@ mf_status mf_batch_get_triggers(mf_batch_t batch, mf_batch_trigger* out, int64_t
 
 /* ---- filtering without device allocation ------------------------------- */
 
-/* The filter of mf_filter (same arithmetic, threshold, window maxima and
- * trigger order) for callers that cannot allocate GPU memory, e.g. code that
- * runs inside another framework's memory pool, a loop that must never
- * allocate, or a plug-in that is only handed buffers.  The paper has no
- * counterpart: it is an interface convenience of this library.
+/* The matched filter of mf_filter for callers that cannot allocate GPU
+ * memory, e.g. code that runs inside another framework's memory pool, a loop
+ * that must never allocate, or a plug-in that is only handed buffers.  The
+ * paper has no counterpart: it is an interface convenience of this library.
+ * The threshold (inclusive), window rule and trigger order are mf_filter's;
+ * the kernels are the per-thread-load filter (k_pass1 / k_pass2, 1/sigma
+ * applied per sample) rather than mf_filter's (pre-scaled data and a
+ * per-template raw threshold), so SNR agrees with mf_filter to 1e-4 relative
+ * and a window peak or a sample at the threshold can differ at near-ties.
  *
  * No plan, no allocation: all working memory lives in one 32 MiB __device__
  * array compiled into the library (present on every GPU that loads it, until
@@ -506,9 +510,10 @@ mf_status mf_batch_get_triggers(mf_batch_t batch, mf_batch_trigger* out, int64_t
  *   trig:   device mf_trigger [trig_cap] (out), count: device int64 (out) =
  *           number found (may exceed trig_cap; only trig_cap are written)
  * Asynchronous on cuda_stream.  All calls share the one array: calls that
- * overlap on the GPU race, so serialise them.  The first call on a device
- * looks up the array's device address, so make it before any stream capture.
- * Errors are reported through mf_last_error(NULL). */
+ * overlap on the GPU race, so serialise them; each call re-initialises what
+ * must start at zero.  Each call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, a host-side query).  Errors are reported
+ * through mf_last_error(NULL). */
 mf_status mf_filter_noalloc(double fs, int64_t n, int32_t n_det, double f_low, double f_high, double snr_thr,
                             int64_t window, const double* psd, const void* htilde, int64_t n_tmpl, int64_t ld_h,
                             const void* dtilde, int64_t ld_d, mf_trigger* trig, int64_t trig_cap, int64_t* count,

@@ -239,6 +239,14 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
       // the consumers' last items are done: then let the next kernel launch
       for (int m = k - 2; ok && m < k; ++m)
         if (m >= 0) ok = mbar_wait_bounded(empty + (m & 1), (uint32_t)((m >> 1) & 1), a.status);
+      if (!ok) {
+        // a wait gave up: before the CTA exits, wait (bounded again) for the copies this lane issued
+        // that no consumer may have waited for (the twiddles and the last two items' tiles); no later
+        // copy went into those slots, so their phases cannot have wrapped
+        mbar_wait_bounded(twb, 0, nullptr);
+        for (int m = k - 2; m < k; ++m)
+          if (m >= 0) mbar_wait_bounded(full + (m & 1), (uint32_t)((m >> 1) & 1), nullptr);
+      }
       pdl_launch_dependents();
     }
     return;
@@ -360,7 +368,13 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
     fence_proxy_async_global_fwd();
     if ((int)blockIdx.x < n_items) issue(blockIdx.x, 0);
   }
-  if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) return;
+  if (__syncthreads_or(!mbar_wait_bounded(bar + 2, 0, a.status))) {
+    if (tid == 0) {  // drain (bounded) the copies issued above before the CTA exits
+      mbar_wait_bounded(bar + 2, 0, nullptr);
+      if ((int)blockIdx.x < n_items) mbar_wait_bounded(bar + 0, 0, nullptr);
+    }
+    return;
+  }
   RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, a.q_type == kBankF32 ? nullptr : a.dscale, a.pos0, a.n_det, a.window,
             a.valid_begin, a.valid_end, a.n_win, a.n_sel_total, a.slots, a.row_valid};
   int k = 0;
@@ -373,7 +387,12 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
     float2 v[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r) v[r] = stage[(t + r * RB) * RW + row];
-    if (__syncthreads_or(fail)) return;
+    if (__syncthreads_or(fail)) {
+      // the copy into this slot may still be in flight: wait for it (bounded) before the CTA exits;
+      // nothing was issued into the other slot since its last wait completed
+      if (tid == 0) mbar_wait_bounded(bar + slot, (uint32_t)((k >> 1) & 1), nullptr);
+      return;
+    }
     if (tid == 0 && item + (int)gridDim.x < n_items) {
       fence_proxy_async();
       issue(item + gridDim.x, slot ^ 1);

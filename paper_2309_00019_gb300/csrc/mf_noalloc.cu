@@ -5,12 +5,15 @@
 // of its working memory in one file-scope __device__ array and allocates
 // nothing on the device or the host.
 //
-// The array (kNoAllocBytes) is a host-side stand-in in host code: its device
-// address is fetched once per device with cudaGetSymbolAddress (on the first
-// call with that device current) and handed to the kernels.  Every call
-// shares the array, so calls that overlap on the GPU (different streams or
-// threads) race; serialise them.  The first call on a device does the
-// address lookup, so make it before any stream capture.
+// In host code the array (kNoAllocBytes) is only a host-side stand-in, not a
+// device address.  Every call therefore asks the runtime for the array's
+// address on the current device (cudaGetSymbolAddress, a host-side query
+// that enqueues no work) and hands that pointer to the kernels.  Looking it
+// up on every call, instead of caching it, keeps it right after the device's
+// context is torn down and created again (cudaDeviceReset), when the module
+// is reloaded and the array can move, and needs no shared host state between
+// caller threads.  Every call shares the array, so calls that overlap on the
+// GPU (different streams or threads) race; serialise them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,11 +26,8 @@
 namespace {
 
 constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB on every device that loads the library
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -70,19 +70,12 @@ extern "C" mf_status mf_filter_noalloc(double fs, int64_t n, int32_t n_det, doub
   if (n_win > 256) return fail(MF_EINVAL, "mf_filter_noalloc: more than 256 windows per segment");
   if (ld_h < nb || ld_d < nb || trig_cap < 1) return fail(MF_EINVAL, "mf_filter_noalloc: leading dimension / capacity");
 
-  // ---- the static array's device address, once per device ----
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(MF_ECUDA, std::string("mf_filter_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(MF_EINVAL, "mf_filter_noalloc: device index out of range");
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(MF_ECUDA, std::string("mf_filter_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  // ---- the static array's address on the current device (looked up on every call) ----
+  void* addr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+  if (e != cudaSuccess || !addr)
+    return fail(MF_ECUDA, std::string("mf_filter_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* base = static_cast<unsigned char*>(addr);
 
   // ---- carve the array ----
   const int64_t ld_q = (nb + 63) / 64 * 64;

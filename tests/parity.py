@@ -89,3 +89,27 @@ def compare_triggers(gpu, rho2, tmpl_ids, thr, window, valid_begin=0, valid_end=
                     assert dphi <= phase_atol, f"phase mismatch {g['phase']} vs {ph}"
     assert not got, f"triggers for templates/windows not expected: {list(got)[:5]}"
     return dict(exact=n_exact, tie_swaps=n_tie_swap, edge=n_edge, max_rel_snr=max_rel)
+
+
+def _coincide_group(args):
+    trig, ring_begin, ring_end, shift_samples, n_shifts, window_samples, rho_c_thr = args
+    return O.coincide(trig, ring_begin, ring_end, shift_samples, n_shifts, window_samples, rho_c_thr=rho_c_thr)
+
+
+def coincide_all_cores(trig, ring_begin, ring_end, shift_samples, n_shifts, window_samples, rho_c_thr,
+                       n_workers=None):
+    """The oracle's coincide over a large trigger list, split by template across
+    a spawn-started process pool (coincidences never pair two templates, so the
+    split is exact); result sorted as coincide sorts it."""
+    import multiprocessing as mp
+    import os
+
+    tm = np.unique(trig["tmpl"])
+    n_workers = max(1, min(n_workers or os.cpu_count() or 1, len(tm)))
+    groups = [trig[np.isin(trig["tmpl"], g)] for g in np.array_split(tm, 4 * n_workers) if len(g)]
+    jobs = [(g, ring_begin, ring_end, shift_samples, n_shifts, window_samples, rho_c_thr) for g in groups]
+    with mp.get_context("spawn").Pool(n_workers) as pool:
+        parts = pool.map(_coincide_group, jobs)
+    parts = [p for p in parts if len(p)]
+    out = np.concatenate(parts) if parts else np.zeros(0, O.COINC_DTYPE)
+    return np.sort(out, order=["tmpl", "shift", "sample0", "sample1"])

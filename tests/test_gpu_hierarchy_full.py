@@ -3,16 +3,21 @@ two detectors x 512 s at 2048 Hz, 2,000 coarse templates at 512 Hz
 (N = 2^18) and 20,000 fine templates at 2048 Hz (N = 2^20) filtered on the
 neighbourhood union (Sec. III).  One hierarchy step is checked on samples the
 FP64 oracle computes one by one (coarse and fine templates, all their
-triggers) and, exactly, on the follow-up logic: every followed coarse
-template has a coincidence over the ranking threshold, and the stage-2 subset
-is the union of the followed templates' neighbourhoods."""
+triggers); the oracle's coincidence search (zero lag and 101 shifts) runs on
+the step's full stage-1 trigger list and must give the same coincidences as
+the GPU, apart from network SNRs at the ranking threshold; and, exactly, on
+the follow-up logic: every followed coarse template has a coincidence over
+the ranking threshold, and the stage-2 subset is the union of the followed
+templates' neighbourhoods."""
+
+import math
 
 import numpy as np
 import pytest
 
 import synth
 from oracle import mf_oracle as O
-from tests.parity import compare_triggers, oracle_rho2
+from tests.parity import coincide_all_cores, compare_triggers, oracle_rho2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,6 +56,29 @@ def test_config2_full_size_sampled(lib):
     assert set(np.unique(over["tmpl"]).tolist()) == set(followed.tolist())
     assert np.array_equal(np.sort(subset), O.nbhd_union(followed, c.nbhd_ptr, c.nbhd_idx))
 
+    # the oracle's coincidences on the same full-size stage-1 triggers.  A pair can reach rho_c >= thr only if
+    # rho_0^2 >= thr^2 - max(rho_1^2 of the template) and vice versa, so triggers failing that (with a margin
+    # for FP32 rounding) cannot take part and are left out of the oracle's input
+    thr2c = c.rho_c_thr ** 2 * (1 - 1e-5)
+    o = trig1.astype(O.TRIGGER_DTYPE) if trig1.dtype != O.TRIGGER_DTYPE else trig1
+    r2 = o["snr"].astype(np.float64) ** 2
+    mx = np.zeros((2, len(c.coarse_m1)))
+    for d in range(2):
+        m = o["det"] == d
+        np.maximum.at(mx[d], o["tmpl"][m], r2[m])
+    keep = r2 >= thr2c - mx[1 - o["det"], o["tmpl"]]
+    ref_co = coincide_all_cores(o[keep], 0, c.n1, int(round(c.shift_s * c.fs1)), c.n_shifts,
+                                int(math.floor(c.coinc_s * c.fs1 + 1e-9)), c.rho_c_thr * (1 - 1e-5))
+    key = lambda x: (int(x["tmpl"]), int(x["shift"]), int(x["sample0"]), int(x["sample1"]))
+    got_c = {key(x): float(x["rho_c"]) for x in co}
+    want_c = {key(x): float(x["rho_c"]) for x in ref_co}
+    for k in got_c.keys() ^ want_c.keys():  # only network SNRs at the ranking threshold may differ
+        v = got_c.get(k, want_c.get(k))
+        assert abs(v - c.rho_c_thr) <= 1e-5 * c.rho_c_thr, (k, v)
+    both = got_c.keys() & want_c.keys()
+    assert len(both) > 0 and all(abs(got_c[k] - want_c[k]) <= 1e-6 * want_c[k] for k in both)
+    assert np.any(co["shift"] == 0) and np.any(co["shift"] > 0)
+
     s2 = O.strain_to_fd(c.strain.astype(np.float64), c.fs2)
     s1 = O.decimate_fd(s2, c.n1)
 
@@ -61,12 +89,20 @@ def test_config2_full_size_sampled(lib):
     rho2, _ = oracle_rho2(s1, rows1.astype(np.complex128), c.psd1, c.n1, c.fs1, c.f_low, c.fs1 / 2)
     st1 = compare_triggers(trig1[np.isin(trig1["tmpl"], ids1)], rho2, ids1, c.thr1, c.window1)
 
-    # stage 2: the first, a middle and the last template of the union
-    ids2 = sorted({int(subset.min()), int(np.sort(subset)[len(subset) // 2]), int(subset.max())})
-    rows2 = synth.taylorf2_torch(c.n2, c.fs2, c.fine_m1[ids2], c.fine_m2[ids2], c.f_low, dev).cpu().numpy()
-    rho2, _ = oracle_rho2(s2, rows2.astype(np.complex128), c.psd2, c.n2, c.fs2, c.f_low, c.fs2 / 2)
-    st2 = compare_triggers(trig2[np.isin(trig2["tmpl"], ids2)], rho2, ids2, c.thr2, c.window2)
-    assert st1["exact"] > 0 and st2["exact"] > 0
-    print(f"\nconfig 2 full size: {n1} stage-1 triggers, {nco} coincidences, {len(followed)} followed, "
-          f"union {n_union}, {n2} stage-2 triggers; oracle samples: stage 1 {ids1} {st1}, stage 2 {ids2} {st2}")
+    # stage 2: 32 templates spread evenly over the sorted union (its first and last included), 8 at a time
+    su = np.sort(subset)
+    ids2 = sorted({int(su[i]) for i in np.linspace(0, len(su) - 1, 32).astype(int)})
+    st2 = dict(exact=0, tie_swaps=0, edge=0, max_rel_snr=0.0)
+    for b in range(0, len(ids2), 8):
+        part = ids2[b:b + 8]
+        rows2 = synth.taylorf2_torch(c.n2, c.fs2, c.fine_m1[part], c.fine_m2[part], c.f_low, dev).cpu().numpy()
+        rho2, _ = oracle_rho2(s2, rows2.astype(np.complex128), c.psd2, c.n2, c.fs2, c.f_low, c.fs2 / 2)
+        st = compare_triggers(trig2[np.isin(trig2["tmpl"], part)], rho2, part, c.thr2, c.window2)
+        for k in ("exact", "tie_swaps", "edge"):
+            st2[k] += st[k]
+        st2["max_rel_snr"] = max(st2["max_rel_snr"], st["max_rel_snr"])
+    assert st1["exact"] > 0 and st2["exact"] > 0 and len(ids2) >= 30
+    print(f"\nconfig 2 full size: {n1} stage-1 triggers, {nco} coincidences ({len(both)} equal to the oracle's), "
+          f"{len(followed)} followed, union {n_union}, {n2} stage-2 triggers; oracle samples: stage 1 {ids1} "
+          f"{st1}, stage 2 {len(ids2)} templates {st2}")
     h.close()
