@@ -107,7 +107,10 @@ def test_noalloc_largest_layout_many_batches(lib):
     psd, bank, fd = _inputs(31, n, fs, 1000, 2, inj=777)
     got, n_got = _noalloc(lib, fs, n, 2, fs / 2, thr, window, psd, bank, fd, 1 << 18)
     assert n_got == len(got) > 0
-    assert len(np.unique(got["tmpl"])) > 900  # templates from every batch fired
+    # templates of every batch (about 30 templates each) fired
+    fired = np.zeros(1000, dtype=bool)
+    fired[got["tmpl"]] = True
+    assert fired.sum() > 800 and all(fired[b:b + 25].any() for b in range(0, 1000, 25))
     st = _against_oracle(got, fd, bank, psd, n, fs, fs / 2, thr, window)
     assert st["exact"] > 0
     print(f"\nN = 2^16, 1000 templates: {n_got} triggers, oracle {st}")
