@@ -39,7 +39,7 @@ WORKLOAD = ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000
             "fine 20000 @ 2048 Hz (N=2^20) on the nbhd union")
 FP32_LANES_PER_SM = 128
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
-KERNEL_NAMES = {2: ("k_cols", "k_rows")}
+KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols", "k_rows_tc")}
 
 
 def measured_traffic(kernel, series_per_launch):
@@ -78,12 +78,16 @@ def parse():
                     help="instead of the benchmark, run two mf_filter calls on a 2-detector plan with N = 2^LOG2N "
                          "(a small, fixed case for profiler captures) and exit")
     ap.add_argument("--kernel-templates", type=int, default=16)
+    ap.add_argument("--intermediate", choices=["f32", "f16"], default="f32",
+                    help="pass-1 -> pass-2 intermediate of the N = 2^20 filter: f32 (ALU row pass) or f16 "
+                         "(tensor-core row pass, SNR within 1e-3)")
     return ap.parse_args()
 
 
-def kernel_case(lg, n_tmpl):
+def kernel_case(lg, n_tmpl, inter="f32"):
     """Two filter calls of a 2-detector, n_tmpl-template plan at N = 2^lg (TaylorF2 bank,
-    coloured noise); used as the fixed workload of profiler captures."""
+    coloured noise); used as the fixed workload of profiler captures.  Prints the
+    per-launch times of the two passes of the second call (CUDA events)."""
     import torch
 
     import synth
@@ -101,12 +105,23 @@ def kernel_case(lg, n_tmpl):
     p = mf.Plan(fs, n, 2, 30.0, fs / 2, 4.0, int(fs))
     p.set_psd(synth.psd_bins(n, fs))
     p.load_bank(bank)
+    if inter == "f16":
+        p.set_intermediate(mf.MF_F16)
     d = torch.from_numpy(fd).to(dev)
-    for _ in range(2):
-        p.filter(d)
+    p.filter(d)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_case": lg, "templates": n_tmpl, "triggers": p.triggers()[1],
-                      "impl": p.stats()["impl"], "batch": p.stats()["batch"]}))
+    p.stats(reset=True)
+    p.profile(True)
+    p.filter(d)
+    torch.cuda.synchronize()
+    st = p.stats(reset=True)
+    p.profile(False)
+    L = max(st["pass1_launches"], 1)
+    print(json.dumps({"kernel_case": lg, "templates": n_tmpl, "triggers": p.triggers()[1], "impl": st["impl"],
+                      "batch": st["batch"], "launches": st["pass1_launches"],
+                      "pass1_ms_per_launch": st["pass1_ms"] / L, "pass2_ms_per_launch": st["pass2_ms"] / L,
+                      "series_per_launch": st["pass1_series"] / L,
+                      "us_per_series": 1e3 * (st["pass1_ms"] + st["pass2_ms"]) / max(st["pass1_series"], 1)}))
     p.close()
     return 0
 
@@ -325,7 +340,7 @@ def reference_arm(args, rank, world):
 def main():
     args = parse()
     if args.kernel_case:
-        return kernel_case(args.kernel_case, args.kernel_templates)
+        return kernel_case(args.kernel_case, args.kernel_templates, args.intermediate)
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
@@ -351,6 +366,8 @@ def main():
     hp = HierParams.from_config(cfg)
     h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), cfg.nbhd_ptr, cfg.nbhd_idx,
                   device=dev)
+    if args.intermediate == "f16":
+        h.p2.set_intermediate(mf.MF_F16)
     for r0, rows in synth.taylorf2_chunks_torch(cfg.n1, cfg.fs1, cfg.coarse_m1, cfg.coarse_m2, cfg.f_low, dev,
                                                 chunk=256, ld=h.ld1):
         h.set_bank_rows(1, r0, rows)
@@ -505,8 +522,11 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.intermediate == "f32" else "f32 + f16 (f16 intermediate and tensor-core operands)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.small else "scaled-down 32 s hierarchy (check run)",
+                       "stage2_intermediate": args.intermediate,
                        "union_templates": int(statistics.mean(unions)),
                        "td_seconds_per_step": td_total / args.steps,
                        "l2": "512 MB buffer written between timed steps; banks (1 GB + 84 GB) streamed from HBM",

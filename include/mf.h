@@ -179,6 +179,21 @@ mf_status mf_set_data_dtype(mf_plan_t plan, mf_dtype dtype);
  * implementation switch to the TMA-staged one.  Errors: MF_EINVAL, MF_ENOMEM. */
 mf_status mf_set_row_valid(mf_plan_t plan, const int64_t* range);
 
+/* Storage of the pass-1 -> pass-2 intermediate of mf_filter (Sec. V.C: the
+ * FFT over coalescence time, here N = N1 N2 in two passes).  MF_F32
+ * (default): complex64, and the row pass runs on the FP32 ALUs.  MF_F16
+ * (N = 2^20 only): complex FP16, each series scaled by a power of two that
+ * puts its values near RMS sqrt(2 / N2), in 8-row panels, and the row pass
+ * runs on the tensor cores: each 1024-point row transform is two radix-32
+ * stages, each a product with the 32 x 32 DFT matrix (FP16 operands, FP32
+ * accumulation in tensor memory).  This halves the intermediate's HBM round
+ * trip and moves the row transforms off the ALUs; SNR then agrees with the
+ * FP64 filter to a few 1e-4 relative (within 1e-3) instead of 1e-6, so the
+ * threshold and window peaks can differ at near-ties of that size.  Needs
+ * FP32 weighted data (MF_F32 data dtype).  Synchronises.  Errors: MF_EINVAL
+ * (dtype, or MF_F16 with N != 2^20). */
+mf_status mf_set_intermediate(mf_plan_t plan, mf_dtype dtype);
+
 /* Templates per pass-1/pass-2 launch pair (the batch; default: as many as
  * fit a 1 GB intermediate).  Reallocates the intermediate (batch x n_det x
  * N x 8 bytes).  Errors: MF_EINVAL (batch < 1), MF_ENOMEM. */
@@ -236,7 +251,8 @@ typedef struct {
   double pass1_ms;
   int64_t pass2_launches, pass2_series;
   double pass2_ms;
-  int32_t impl;       /* filter kernels in use: 2 = TMA-staged k_cols / k_rows (the only ones) */
+  int32_t impl;       /* filter kernels in use: 2 = k_cols / k_rows (FP32 intermediate), 3 = k_cols /
+                         k_rows_tc (FP16 intermediate, tensor-core row pass) */
   int32_t batch;      /* templates per pass-1 / pass-2 launch pair */
 } mf_plan_stats;
 

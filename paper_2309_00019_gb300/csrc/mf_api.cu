@@ -42,6 +42,7 @@ struct mf_plan_s {
   float2* q = nullptr;
   int64_t ld_q = 0;
   mf_dtype data_dtype = MF_F32;   // storage of the weighted data the filter reads
+  bool inter_f16 = false;         // FP16 pass-1 -> pass-2 intermediate and the tensor-core row pass
   void* q_lp = nullptr;           // 16-bit weighted data [n_det][ld_q]
   unsigned* dmax = nullptr;       // per-detector max |q| (float bits)
   float* dscale = nullptr;        // per-detector power-of-two data scale
@@ -108,6 +109,7 @@ uint64_t plan_fingerprint(const mf_plan_s* p) {
   mix((uint64_t)p->n_tmpl);
   mix((uint64_t)p->batch);
   mix((uint64_t)p->data_dtype);
+  mix((uint64_t)p->inter_f16);
   mix((uint64_t)(uintptr_t)p->row_valid);
   mix((uint64_t)(uintptr_t)p->scratch);
   mix((uint64_t)(uintptr_t)p->slots);
@@ -476,6 +478,16 @@ mf_status mf_set_data_dtype(mf_plan_t p, mf_dtype dtype) {
   return MF_OK;
 }
 
+mf_status mf_set_intermediate(mf_plan_t p, mf_dtype dtype) {
+  if (!p) return fail(p, MF_EINVAL, "mf_set_intermediate: null plan");
+  if (dtype != MF_F32 && dtype != MF_F16) return fail(p, MF_EINVAL, "mf_set_intermediate: dtype must be F32 or F16");
+  if (dtype == MF_F16 && p->d.n != (int64_t(1) << 20))
+    return fail(p, MF_EINVAL, "mf_set_intermediate: the FP16 intermediate needs N = 2^20");
+  cudaStreamSynchronize(p->st);
+  p->inter_f16 = dtype == MF_F16;
+  return MF_OK;
+}
+
 mf_status mf_set_row_valid(mf_plan_t p, const int64_t* range) {
   if (!p) return fail(p, MF_EINVAL, "mf_set_row_valid: null plan");
   cudaStreamSynchronize(p->st);
@@ -575,6 +587,8 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   if (n_subset > 0 && !subset) return fail(p, MF_EINVAL, "mf_filter: subset is NULL");
   if (p->data_dtype != MF_F32 && p->data_dtype != p->bank_dtype)
     return fail(p, MF_EINVAL, "mf_filter: 16-bit data need a bank of the same 16-bit type");
+  if (p->inter_f16 && p->data_dtype != MF_F32)
+    return fail(p, MF_EINVAL, "mf_filter: the FP16 intermediate needs FP32 weighted data");
   const int64_t n_sel = n_subset < 0 ? p->n_tmpl : n_subset;
   mf_status s = ensure_slots(p, std::max<int64_t>(n_sel, 1));
   if (s != MF_OK) return s;
@@ -626,6 +640,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.q_type = bank_type(p->data_dtype);
   a.q_lp = p->q_lp;
   a.dscale = p->dscale;
+  a.inter_f16 = p->inter_f16 ? 1 : 0;
   LaunchScope ls(p);
   ls.before = launches_before;
   for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
@@ -684,7 +699,7 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     p->stats.pass2_ms += t2;
   }
   p->samples.clear();
-  p->stats.impl = 2;
+  p->stats.impl = p->inter_f16 ? 3 : 2;
   p->stats.batch = p->batch;
   *out = p->stats;
   if (reset) p->stats = mf_plan_stats{};

@@ -45,6 +45,18 @@ struct BankElem<kBankBF16> {
   }
 };
 
+// Power-of-two scale of one series of the FP16 intermediate: 2^(e-1) with ratio = m 2^e, m in [0.5, 1),
+// so that ratio / scale is in [1, 2).  ratio = sigma_ref / sigma of the template; the pre-scaled data give
+// pass-1 outputs of RMS ~ sqrt(2 / N2) / ratio in Gaussian noise, so the scaled ones sit near sqrt(2 / N2)
+// whatever the template (far inside FP16's normal range).  The row pass divides it out of rho exactly.
+__device__ __forceinline__ float series_scale16(float ratio) {
+  if (!(ratio > 0.f) || !isfinite(ratio)) return 1.f;
+  int e = 0;
+  frexpf(ratio, &e);
+  e = max(-24, min(24, e - 1));
+  return ldexpf(1.f, e);
+}
+
 // Record a sample that passed the threshold: packed (rho^2, sample, phase)
 // atomic maximum into its window slot.  Out of line: it runs for a small
 // fraction of samples and keeping it out of the unrolled hot loop keeps that

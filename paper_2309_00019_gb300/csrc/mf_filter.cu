@@ -178,14 +178,18 @@ __global__ void k_fill_twiddles(float2* tw) {
 // pass 1
 // ---------------------------------------------------------------------------
 
-template <int N1, int N2, int BT, int QT>
+// H16: FP16 intermediate, each series scaled by series_scale16 of its template, in panels of kPanel16
+// rows that are the tensor-core row pass's stage-1 operand image: with k2 = 32 p + q, part c (0 real,
+// 1 imaginary) of element (j1, k2) is the half at panel j1 / 8, ((q 32 + p) 2 + c) 8 + j1 % 8 (panels of
+// 2 N2 8 halves), i.e. the MN-major layout of rows m = 8 q + j1 % 8 and columns k = 2 p + c
+template <int N1, int N2, int BT, int QT, bool H16>
 __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   using G = SubFft<N1>;
   using P = ColGeo<N1, BT, QT>;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
   constexpr int NCB = N2 / C;
   constexpr uint32_t N = (uint32_t)N1 * (uint32_t)N2;
-  constexpr int PH = ScratchGeo<N1, N2>::P;  // scratch panel height
+  constexpr int PH = H16 ? kPanel16 : ScratchGeo<N1, N2>::P;  // scratch panel height
   extern __shared__ __align__(128) unsigned char sm[];
   const float2* tw = reinterpret_cast<const float2*>(sm + P::TW_OFF);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + P::BAR_OFF);  // [0], [1]: tiles of the slot landed
@@ -278,7 +282,10 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
     __syncwarp();
     float2* out = a.scratch + (int64_t)s * N;
+    __half* out16 = reinterpret_cast<__half*>(a.scratch) + (int64_t)s * 2 * N;
     const int k2 = ((item / a.n_det) % NCB) * C + ca;
+    float sc = 1.f;
+    if constexpr (H16) sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + item / (a.n_det * NCB)]));
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = ta + T * i;
@@ -292,7 +299,27 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
       const float2* twr = a.tw4 + (int64_t)k2 * (RA + 1);
       float2 w = __ldg(twr + j);
       const float2 st = __ldg(twr + RA);
-      if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
+      if constexpr (H16) {
+        static_assert(RA % PH == 0 && N2 == 1024, "FP16 panels");
+        w.x *= sc;
+        w.y *= sc;
+        // j1 = j + q RA: q RA / 8 whole panels past j's; within a panel, (k2 % 32, k2 / 32, part, j1 % 8).
+        // Lanes j, j + 1 (j even) of the column swap halves so that each writes 4 bytes: j the real parts
+        // of rows j, j + 1 and j + 1 their imaginary parts (one warp store: four whole 32-byte sectors)
+        static_assert(T == 32, "lane pairs");
+        const bool odd = (j & 1) != 0;
+        __half* ob = out16 + (int64_t)(j / PH) * (2 * N2 * PH) + (((k2 & 31) * 32 + (k2 >> 5)) * 2) * PH +
+                     (odd ? PH + (j % PH) - 1 : (j % PH));
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const __half2 h = __float22half2_rn(cmul(u[q], w));
+          const uint32_t mine = *reinterpret_cast<const uint32_t*>(&h);
+          const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+          const uint32_t v = odd ? __byte_perm(other, mine, 0x7632) : __byte_perm(mine, other, 0x5410);
+          *reinterpret_cast<uint32_t*>(ob + (int64_t)q * (RA / PH) * (2 * N2 * PH)) = v;
+          if (q + 1 < RB) w = cmul(w, st);
+        }
+      } else if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
         float2* ob = out + (int64_t)(j / PH) * (N2 * PH) + k2 * PH + (j % PH);
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
@@ -455,11 +482,11 @@ int grid2(int items) {
   return items < g ? items : g;
 }
 
-template <int N1, int N2, int BT, int QT>
+template <int N1, int N2, int BT, int QT, bool H16 = false>
 cudaError_t run_cols(const FilterArgs& a, cudaStream_t st) {
   using P = ColGeo<N1, BT, QT>;
   static_assert(P::SMEM * 3 <= 230400, "k_cols: three CTAs per SM must fit in shared memory");
-  auto k = k_cols<N1, N2, BT, QT>;
+  auto k = k_cols<N1, N2, BT, QT, H16>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem2(k, P::SMEM);
@@ -475,6 +502,19 @@ cudaError_t run_cols(const FilterArgs& a, cudaStream_t st) {
 // (bank, data) storage pairs: FP32 data with any bank; 16-bit data with a bank of the same type
 template <int N1, int N2>
 cudaError_t run_cols_bt(const FilterArgs& a, cudaStream_t st) {
+  if constexpr (N1 == 1024 && N2 == 1024) {
+    if (a.inter_f16) {  // FP16 intermediate for the tensor-core row pass: FP32 data, any bank
+      if (a.q_type != kBankF32) return cudaErrorInvalidValue;
+      switch (a.bank_type) {
+        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, true>(a, st);
+        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, true>(a, st);
+        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, true>(a, st);
+      }
+      return cudaErrorInvalidValue;
+    }
+  } else {
+    if (a.inter_f16) return cudaErrorInvalidValue;
+  }
   if (a.q_type == kBankF32) {
     switch (a.bank_type) {
       case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32>(a, st);
@@ -590,6 +630,7 @@ cudaError_t tw4_count_of(int64_t* c) {
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH2(a.n, run_cols_bt, (a, st)) }
 
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
+  if (a.inter_f16) return launch_filter2_pass2_tc(a, st);
   MF_DISPATCH2(a.n, run_rows, (a, tm, st))
 }
 

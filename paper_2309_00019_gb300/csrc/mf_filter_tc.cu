@@ -1,0 +1,322 @@
+// Tensor-core row pass of the matched filter (Eq. 1-2, Sec. V.C: the inverse
+// transform over coalescence time), N = N1 N2 with N2 = 1024, over the FP16
+// pass-1 -> pass-2 intermediate that k_cols writes in 8-row panels.
+//
+// A row x[k2] (k2 = 32 p + q) has the 1024-point transform
+//   z[u + 32 v] = sum_q w32^{q v} w1024^{q u} Y[u][q],   Y[u][q] = sum_p w32^{p u} x[32 p + q],
+// (w_M = exp(+2 pi i / M)): two radix-32 stages, each a product with the
+// complex 32 x 32 DFT matrix, which is a dense contraction and runs on the
+// tensor cores as a real 64 x 64 matrix (real and imaginary parts interleaved
+// along K and N) with FP16 operands and FP32 accumulation in tensor memory:
+//   stage 1: D1[(q, r)][(u, c)] = sum_(p, c') A1[(q, r)][(p, c')] B[(u, c)][(p, c')]
+//   stage 2: D2[(u, r)][(v, c)] = sum_(q, c') A2[(u, r)][(q, c')] B[(v, c)][(q, c')]
+// with B the embedded DFT matrix, A1 a panel of 8 rows (r) exactly as k_cols
+// stored it (the MN-major operand image, one 32 KB bulk copy) and A2 the
+// stage-1 result times w1024^{q u}, rounded to FP16 (K-major).  M = 256 rows
+// per stage, as two M = 128 tiles.
+//
+// One persistent CTA per SM, 576 threads.  Warp 16 copies items into six
+// shared-memory slots; a slot holds its item's stage-1 operand and then (written
+// over it) its stage-2 operand, and is free again once stage 2 has read it.
+// Warp 17 owns all 512 tensor-memory columns (four buffers of 2 x 64) and one
+// lane issues the MMAs in an event loop: stage 1 of item k when its slot has
+// landed and its buffer is free, stage 2 when its operand is written, in item
+// order each.  Warps 0-15 are four consumer groups; group g takes items
+// k = g, g + 4, ... in buffer g.  In a group, thread t = TMEM lane t of both
+// tiles (q or u = t / 8 + 16 h, r = t % 8 for tile h) applies the twiddles
+// between the stages and runs the epilogue (raw |z|^2 against the
+// per-template threshold, window maxima) on the stage-2 accumulators.
+// Barriers: per slot full / a2full / empty, per buffer d1 / d2 / tfree, and
+// a drain barrier; every wait is bounded.
+#include "mf_common.cuh"
+#include "mf_tc.cuh"
+#include "mf_tma.cuh"
+
+namespace mf {
+
+namespace {
+
+constexpr int kGroup = 128;                       // threads of one consumer group
+constexpr int kGroups = 4;
+constexpr int kTcThreads = kGroups * kGroup + 64; // + producer warp + MMA warp
+constexpr int kProdWarp = kGroups * 4, kMmaWarp = kProdWarp + 1;
+constexpr int kTcRows = kPanel16;                 // rows per item
+constexpr int kTcK = 64;                          // 32 complex values, real and imaginary interleaved
+constexpr int kLbo = 128, kSbo = 1024;            // unpadded core-matrix layouts
+constexpr int kTileBytes = 128 * kTcK * 2;        // one M = 128 operand tile, 16 KB
+constexpr int kItemBytes = 2 * kTileBytes;        // one item (256 rows), 32 KB
+constexpr int kSlots = 6;                         // operand slots
+constexpr int kB_OFF = kSlots * kItemBytes;       // B: 64 x 64, 8 KB
+constexpr int kTwStride = 33;                     // padded rows of the w1024^{q u} table (float2)
+constexpr int kTW_OFF = kB_OFF + 64 * kTcK * 2;
+constexpr int kBAR_OFF = kTW_OFF + 32 * kTwStride * 8;
+constexpr int kNBar = 3 * kSlots + 3 * kGroups + 1;
+constexpr int kSMEM = kBAR_OFF + kNBar * 8 + 16;
+constexpr uint32_t kBufCols = 128;                // 2 tiles x 64 FP32 columns
+constexpr uint32_t kTmemCols = kGroups * kBufCols;  // all 512
+constexpr uint32_t kIdesc2 = tc_idesc_f16(128, 64);          // A K-major (stage 2)
+constexpr uint32_t kIdesc1 = kIdesc2 | (1u << 15);           // A MN-major (stage 1)
+
+static_assert(cm_offset(255, 63, kLbo, kSbo) + 2 <= kItemBytes, "A2 layout");
+static_assert(kSMEM <= 232448, "k_rows_tc shared memory");
+
+// generic-proxy writes of another grid -> async-proxy (bulk copy) reads of this one
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_half2(float re, float im) {
+  __half2 h = __floats2half2_rn(re, im);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// 8 MMAs of one stage: two M = 128 tiles x four K = 16 steps into buffer columns [d, d + 128)
+__device__ __forceinline__ void stage_mmas(uint32_t d, uint32_t a_addr, bool mn_major, uint32_t b_addr) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int ks = 0; ks < kTcK / 16; ++ks) {
+      // K steps: two core matrices along K, 128 B apart in both operand layouts
+      const uint64_t ad = tc_desc(a_addr + h * kTileBytes + ks * 2 * kLbo, kLbo, kSbo);
+      const uint64_t bd = tc_desc(b_addr + ks * 2 * kLbo, kLbo, kSbo);
+      tc_mma_f16(d + 64 * h, ad, bd, mn_major ? kIdesc1 : kIdesc2, ks > 0);
+    }
+}
+
+// parity of the n-th completion (n = 0, 1, ...) of a barrier
+__device__ __forceinline__ uint32_t par(int n) { return (uint32_t)(n & 1); }
+
+template <int N1>
+__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
+  constexpr int N2 = 1024;
+  constexpr int64_t N = (int64_t)N1 * N2;
+  constexpr int NP = N1 / kTcRows;  // panels (items) per series
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sB = sm + kB_OFF;
+  float2* tw = reinterpret_cast<float2*>(sm + kTW_OFF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kBAR_OFF);  // [kSlots]
+  uint64_t* a2full = full + kSlots;                              // [kSlots]
+  uint64_t* empty = a2full + kSlots;                             // [kSlots]
+  uint64_t* d1 = empty + kSlots;                                 // [kGroups]
+  uint64_t* d2 = d1 + kGroups;
+  uint64_t* tfree = d2 + kGroups;
+  uint64_t* drain = tfree + kGroups;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBAR_OFF + kNBar * 8);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const int n_series = a.count * a.n_det;
+  const int n_items = n_series * NP;
+  int n_mine = 0;  // items of this CTA: blockIdx.x + k gridDim.x
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) ++n_mine;
+
+  if (warp == kMmaWarp) tmem_alloc(tslot, kTmemCols);
+  // B: the embedded DFT matrix, B[(u, c)][(p, c')] = Re / Im parts of w32^{p u}
+  for (int i = tid; i < 64 * kTcK; i += kTcThreads) {
+    const int n = i / kTcK, k = i % kTcK, u = n >> 1, c = n & 1, p = k >> 1, cp = k & 1;
+    const float2 f = unit_root((uint32_t)((p * u) & 31), 32u);
+    const float v = c == 0 ? (cp == 0 ? f.x : -f.y) : (cp == 0 ? f.y : f.x);
+    *reinterpret_cast<__half*>(sB + cm_offset(n, k, kLbo, kSbo)) = __float2half_rn(v);
+  }
+  for (int i = tid; i < 32 * 32; i += kTcThreads) {
+    const int q = i >> 5, u = i & 31;
+    tw[q * kTwStride + u] = unit_root((uint32_t)(q * u), 1024u);
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kSlots; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(a2full + i, kGroup);
+      mbar_init(empty + i, 1);
+    }
+    for (int g = 0; g < kGroups; ++g) {
+      mbar_init(d1 + g, 1);
+      mbar_init(d2 + g, 1);
+      mbar_init(tfree + g, kGroup);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const __half* scratch = reinterpret_cast<const __half*>(a.scratch);
+
+  if (warp == kProdWarp) {
+    // ---- producer: item k into slot k % 6 once stage 2 of item k - 6 has read that slot ----
+    if (lane == 0) {
+      pdl_wait();  // the intermediate is written by the kernel just before
+      fence_proxy_async_global();
+      int k = 0;
+      bool ok = true;
+      for (; k < n_mine; ++k) {
+        const int slot = k % kSlots;
+        if (k >= kSlots && !(ok = mbar_wait_bounded(empty + slot, par(k / kSlots - 1), a.status))) break;
+        const int item = blockIdx.x + k * gridDim.x;
+        const int s = n_series - 1 - item / NP;  // series in reverse: the last ones written are likeliest in L2
+        const __half* src = scratch + (int64_t)s * 2 * N + (int64_t)(item % NP) * (2 * N2 * kTcRows);
+        mbar_expect_tx(full + slot, (uint32_t)kItemBytes);
+        bulk_g2s(sm + slot * kItemBytes, src, (uint32_t)kItemBytes, full + slot);
+      }
+      if (!ok)  // copies this lane issued that nobody may have waited for
+        for (int m = k - kSlots; m < k; ++m)
+          if (m >= 0) mbar_wait_bounded(full + (m % kSlots), par(m / kSlots), nullptr);
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issuer: whichever of stage 1 (next item) / stage 2 (oldest item) is ready ----
+    if (lane == 0) {
+      const uint32_t bb = smem_u32(sB);
+      int n1 = 0, n2 = 0;  // items whose stage 1 / stage 2 have been issued
+      bool ok = true;
+      long long t0 = clock64();
+      while (n2 < n_mine) {
+        bool progress = false;
+        if (n1 < n_mine) {
+          const int slot = n1 % kSlots, g = n1 % kGroups;
+          if (mbar_try_wait(full + slot, par(n1 / kSlots)) &&
+              (n1 < kGroups || mbar_try_wait(tfree + g, par(n1 / kGroups - 1)))) {
+            tc_fence_after();
+            stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
+            tc_commit(d1 + g);
+            ++n1;
+            progress = true;
+          }
+        }
+        if (n2 < n1) {
+          const int slot = n2 % kSlots, g = n2 % kGroups;
+          if (mbar_try_wait(a2full + slot, par(n2 / kSlots))) {
+            tc_fence_after();
+            stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
+            tc_commit(d2 + g);
+            tc_commit(empty + slot);
+            ++n2;
+            progress = true;
+          }
+        }
+        if (progress) {
+          t0 = clock64();
+        } else if (clock64() - t0 > (1LL << 31)) {
+          atomicExch(a.status, kStatusTimeout);
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) {  // the MMAs in flight: wait (bounded again) for everything this lane issued to retire
+        tc_commit(drain);
+        mbar_wait_bounded(drain, 0, nullptr);
+      }
+    }
+  } else {
+    // ---- consumer group g = warp / 4: items k = g, g + 4, ...; twiddle, then epilogue ----
+    const int g = warp >> 2, lt = tid & (kGroup - 1);
+    const int r = lt & 7, qg = lt >> 3;
+    const uint32_t tbuf = tmem + g * kBufCols + ((uint32_t)(32 * (warp & 3)) << 16);
+    RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, nullptr, a.pos0, a.n_det, a.window, a.valid_begin, a.valid_end,
+              a.n_win, a.n_sel_total, a.slots, a.row_valid};
+    for (int k = g; k < n_mine; k += kGroups) {
+      const int slot = k % kSlots;
+      unsigned char* sl = sm + slot * kItemBytes;
+      // twiddle w1024^{q u}, round to FP16, stage-2 operand row (u, r), K = (q, c), over the slot
+      if (!mbar_wait_bounded(d1 + g, par(k / kGroups), a.status)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = qg + 16 * h;
+        const float2* twq = tw + q * kTwStride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {  // u = 16 c .. 16 c + 15
+          float y[32];
+          tmem_ld32(tbuf + 64 * h + 32 * c, y);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int u = 16 * c + i;
+            const float2 z = cmul(make_float2(y[2 * i], y[2 * i + 1]), twq[u]);
+            *reinterpret_cast<uint32_t*>(sl + cm_offset(u * 8 + r, 2 * q, kLbo, kSbo)) = pack_half2(z.x, z.y);
+          }
+        }
+      }
+      fence_proxy_async();  // our operand writes before the MMAs that read them
+      mbar_arrive(a2full + slot);
+      // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r
+      if (!mbar_wait_bounded(d2 + g, par(k / kGroups), a.status)) break;
+      tc_fence_after();
+      const int item = blockIdx.x + k * gridDim.x;
+      const int s = n_series - 1 - item / NP;
+      auto se = ep.series(s);
+      {
+        const float sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + s / a.n_det]));
+        se.ratio /= sc;  // exact: sc is a power of two
+        se.thr *= sc * sc;
+      }
+      const int64_t j1 = (int64_t)(item % NP) * kTcRows + r;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = qg + 16 * h;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {  // v = 16 c .. 16 c + 15
+          float z[32];
+          tmem_ld32(tbuf + 64 * h + 32 * c, z);
+          float mx = 0.f;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaf(z[2 * i], z[2 * i], z[2 * i + 1] * z[2 * i + 1]));
+          if (mx >= se.thr) {  // rare: some sample of this row is over the threshold
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              ep(se, j1 + (int64_t)N1 * (u + 32 * (16 * c + i)), make_float2(z[2 * i], z[2 * i + 1]));
+          }
+        }
+      }
+      tc_fence_before();  // our tensor-memory reads before the MMAs that reuse the buffer
+      mbar_arrive(tfree + g);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_free(tmem, kTmemCols);
+  pdl_launch_dependents();
+}
+
+template <class K, class... Args>
+cudaError_t launch_pdl_tc(K kern, int grid, int block, int smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+int sm_count_tc() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st) {
+  if (a.n != (int64_t(1) << 20) || a.n1 != 1024 || a.n2 != 1024 || a.q_type != kBankF32 || !a.inter_f16)
+    return cudaErrorInvalidValue;
+  auto k = k_rows_tc<1024>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int items = a.count * a.n_det * (1024 / kTcRows);
+  const int g = sm_count_tc();  // one CTA (all 512 TMEM columns) per SM
+  cudaError_t e = launch_pdl_tc(k, items < g ? items : g, kTcThreads, kSMEM, st, a);
+  add_launches(1);
+  return e;
+}
+
+}  // namespace mf

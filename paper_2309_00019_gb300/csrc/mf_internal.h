@@ -60,7 +60,13 @@ struct FilterArgs {
   const float* dscale;
   // per data row analysed range [x, y) (TMA kernels), or null: [valid_begin, valid_end) for all rows
   const int2* row_valid;
+  // 1: FP16 pass-1 -> pass-2 intermediate in kPanel16-row panels, each series scaled by
+  // series_scale16(ratio[template]), and the tensor-core row pass (N = 2^20 only)
+  int inter_f16;
 };
+
+// rows per panel of the FP16 intermediate: a panel is one tensor-core row-pass item
+constexpr int kPanel16 = 8;
 
 // Quantise the FP32 weighted data q [n_det][ld_q] (nb bins per detector) to
 // 16-bit (q_type) q_lp with a per-detector power-of-two scale c_d chosen so that
@@ -85,6 +91,8 @@ bool plan_capturable(const ::mf_plan_s* p);
 // half (k1 < N1/2) at k2 N1/2 + k1 (see launch_to_cols).
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& scratch_map, cudaStream_t st);
+// the tensor-core row pass over the FP16 intermediate (mf_filter_tc.cu), N = 2^20
+cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st);
 // Tensor map of the pass-1 -> pass-2 scratch (`series` series of length n)
 // through which pass 2 reads its items; all zero where pass 2 needs none.
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m);

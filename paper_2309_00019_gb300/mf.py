@@ -86,6 +86,7 @@ SIGNATURES = {
     "mf_get_sigmasq": (C.c_int, [_P, _P, _I64]),
     "mf_bank_quantize_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, C.c_int]),
     "mf_set_data_dtype": (C.c_int, [_P, C.c_int]),
+    "mf_set_intermediate": (C.c_int, [_P, C.c_int]),
     "mf_set_row_valid": (C.c_int, [_P, _P]),
     "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mf_chisq": (C.c_int, [_P, C.c_int32, _P, _P]),
@@ -247,6 +248,9 @@ class Plan:
 
     def set_data_dtype(self, dtype):
         _check(self.h, self.lib.mf_set_data_dtype(self.h, dtype))
+
+    def set_intermediate(self, dtype):
+        _check(self.h, self.lib.mf_set_intermediate(self.h, dtype))
 
     def set_row_valid(self, ranges):
         """Per-row analysed ranges, int64 [n_det, 2] (None restores the plan's range)."""
