@@ -719,7 +719,10 @@ mf_status mf_get_triggers(mf_plan_t p, mf_trigger* out, int64_t cap, int64_t* n_
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_triggers status");
   if (dst != 0) {
     cudaMemset(p->status, 0, sizeof(int));
-    return fail(p, MF_ETIMEOUT, "mf_get_triggers: a bounded device wait timed out; results are incomplete");
+    std::string m = "mf_get_triggers: a bounded device wait timed out; results are incomplete";
+    if (dst >> 8)  // waits that record where they gave up: site and item
+      m += " (wait site " + std::to_string((dst >> 8) & 0xff) + ", item " + std::to_string((unsigned)dst >> 16) + ")";
+    return fail(p, MF_ETIMEOUT, m);
   }
   const int64_t m = std::min<int64_t>(std::min<int64_t>(n, cap), p->d.max_triggers);
   if (m > 0) {

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
       bool ok = true;
       for (; k < n_mine; ++k) {
         const int slot = k % kSlots;
-        if (k >= kSlots && !(ok = mbar_wait_bounded(empty + slot, par(k / kSlots - 1), a.status))) break;
+        if (k >= kSlots && !(ok = mbar_wait_at(empty + slot, par(k / kSlots - 1), a.status, 11, k))) break;
         const int item = blockIdx.x + k * gridDim.x;
         const int s = n_series - 1 - item / NP;  // series in reverse: the last ones written are likeliest in L2
         const __half* src = scratch + (int64_t)s * 2 * N + (int64_t)(item % NP) * (2 * N2 * kTcRows);
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
         bool progress = false;
         if (n1 < n_mine) {
           const int slot = n1 % kSlots, g = n1 % kGroups;
-          if (mbar_try_wait(full + slot, par(n1 / kSlots)) &&
-              (n1 < kGroups || mbar_try_wait(tfree + g, par(n1 / kGroups - 1)))) {
+          if (mbar_test_wait(full + slot, par(n1 / kSlots)) &&
+              (n1 < kGroups || mbar_test_wait(tfree + g, par(n1 / kGroups - 1)))) {
             tc_fence_after();
             stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
             tc_commit(d1 + g);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
         }
         if (n2 < n1) {
           const int slot = n2 % kSlots, g = n2 % kGroups;
-          if (mbar_try_wait(a2full + slot, par(n2 / kSlots))) {
+          if (mbar_test_wait(a2full + slot, par(n2 / kSlots))) {
             tc_fence_after();
             stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
             tc_commit(d2 + g);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
         if (progress) {
           t0 = clock64();
         } else if (clock64() - t0 > (1LL << 31)) {
-          atomicExch(a.status, kStatusTimeout);
+          atomicCAS(a.status, 0, kStatusTimeout | ((n1 < n_mine ? 12 : 13) << 8) | ((n1 < n_mine ? n1 : n2) << 16));
           ok = false;
           break;
         }
@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
       const int slot = k % kSlots;
       unsigned char* sl = sm + slot * kItemBytes;
       // twiddle w1024^{q u}, round to FP16, stage-2 operand row (u, r), K = (q, c), over the slot
-      if (!mbar_wait_bounded(d1 + g, par(k / kGroups), a.status)) break;
+      // (warp-uniform outcome: the tensor-memory loads below are warp-collective)
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d1 + g, par(k / kGroups), a.status, 14, k))) break;
       tc_fence_after();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
       fence_proxy_async();  // our operand writes before the MMAs that read them
       mbar_arrive(a2full + slot);
       // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r
-      if (!mbar_wait_bounded(d2 + g, par(k / kGroups), a.status)) break;
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d2 + g, par(k / kGroups), a.status, 15, k))) break;
       tc_fence_after();
       const int item = blockIdx.x + k * gridDim.x;
       const int s = n_series - 1 - item / NP;

@@ -44,14 +44,52 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Spin until the phase with `parity` completes or ~2^31 cycles pass; on
+// Non-blocking test (try_wait may suspend the thread for a while when the phase is incomplete; a thread
+// that polls several barriers in turn wants an immediate answer)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or about 20 us pass,
+// instead of spinning (spinning waiters take issue slots from the warps that do the work)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait until the phase with `parity` completes or ~2^31 cycles pass; on
 // timeout record kStatusTimeout in *status and return false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_try_wait_sleep(bar, parity)) {
     if (clock64() - t0 > (1LL << 31)) {
       if (status) atomicExch(status, kStatusTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+// As mbar_wait_bounded, but a timeout records where it happened: status = 1 | site << 8 | (item & 0xffff) << 16
+// (the first timeout wins), so that the host can report which wait gave up.
+__device__ __forceinline__ bool mbar_wait_at(uint64_t* bar, uint32_t parity, int* status, int site, int item) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) {
+      if (status) atomicCAS(status, 0, kStatusTimeout | (site << 8) | ((item & 0xffff) << 16));
       return false;
     }
   }
