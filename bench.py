@@ -41,7 +41,7 @@ WORKLOAD = ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000
             "fine 20000 @ 2048 Hz (N=2^20) on the nbhd union")
 FP32_LANES_PER_SM = 128
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
-KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols", "k_rows_tc")}
+KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols_h16", "k_rows_tc")}  # k_cols_h16: k_cols with FP16 output
 
 
 def measured_traffic(kernel, series_per_launch):
