@@ -150,6 +150,29 @@ mf_status mf_bank_reserve(mf_plan_t plan, mf_dtype dtype, int64_t n_tmpl);
 mf_status mf_bank_set_rows(mf_plan_t plan, int64_t row0, int64_t n_rows, const void* htilde, int64_t ld,
                            const float* scales, int on_device);
 
+/* TaylorF2 templates generated on the GPU (Sec. II: the bank's waveforms;
+ * the paper does not name them, the bank here is non-spinning TaylorF2 with
+ * the 3.5PN phase of Buonanno et al. 2009, Eq. 3.18, and Newtonian
+ * amplitude): h~(f) = f^{-7/6} exp(-i Psi(f)) for f_low <= f <=
+ * min(f_ISCO, fs/2), bin k < N/2, zero elsewhere, with t_c = phi_c = 0 and
+ * f_ISCO = 1 / (6^{3/2} pi M).  Psi is evaluated in float64 at anchors at most
+ * 0.25 Hz apart and interpolated (cubic) in float32 between them; the
+ * template's match with the float64 formula is 1 to better than 1e-8.
+ *   m1, m2: host float64 [n_tmpl], solar masses (copied)
+ *   out:    device complex64 [n_tmpl][ld], ld >= N/2+1, bins 0..N/2 written
+ * Synchronises cuda_stream.  Errors (mf_last_error(NULL)): MF_EINVAL (sizes,
+ * masses <= 0, f_low <= 0), MF_ECUDA. */
+mf_status mf_taylorf2(const double* m1, const double* m2, int64_t n_tmpl, double fs, int64_t n, double f_low,
+                      void* out, int64_t ld, void* cuda_stream);
+
+/* Generate bank rows [row0, row0+n_rows) of the plan on the GPU (as
+ * mf_taylorf2 at the plan's fs and N, f_low given), store them in the bank's
+ * layout and type (float32, or 16-bit as mf_bank_quantize_rows) and compute
+ * their sigma^2: banks are filled without a host copy of the templates.
+ * Synchronises.  Errors: MF_ESTATE (no bank), MF_EINVAL, MF_ENOMEM, MF_ECUDA. */
+mf_status mf_bank_generate_taylorf2(mf_plan_t plan, int64_t row0, int64_t n_rows, const double* m1, const double* m2,
+                                    double f_low);
+
 /* Reduced-precision storage (no counterpart in the paper, which filters in
  * double precision on CPUs): quantise rows [row0, row0+n_rows) of a 16-bit
  * bank (reserved as MF_F16 or MF_BF16) from float32 complex templates

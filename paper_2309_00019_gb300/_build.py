@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmf.so")
-SOURCES = ["mf_kernels.cu", "mf_filter.cu", "mf_filter_tc.cu", "mf_glue.cu", "mf_api.cu", "mf_noalloc.cu", "mf_mlp.cu", "mf_batch.cu", "mf_chisq.cu", "mf_psd.cu", "mf_gate.cu"]
+SOURCES = ["mf_kernels.cu", "mf_filter.cu", "mf_filter_tc.cu", "mf_glue.cu", "mf_api.cu", "mf_noalloc.cu", "mf_mlp.cu", "mf_batch.cu", "mf_chisq.cu", "mf_psd.cu", "mf_gate.cu", "mf_taylorf2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall", "-cudart", "shared", "-I", os.path.join(ROOT, "include")]

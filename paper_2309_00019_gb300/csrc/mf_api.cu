@@ -478,6 +478,36 @@ mf_status mf_set_data_dtype(mf_plan_t p, mf_dtype dtype) {
   return MF_OK;
 }
 
+mf_status mf_bank_generate_taylorf2(mf_plan_t p, int64_t row0, int64_t n_rows, const double* m1, const double* m2,
+                                    double f_low) {
+  if (!p || !m1 || !m2) return fail(p, MF_EINVAL, "mf_bank_generate_taylorf2: null argument");
+  if (!p->bank) return fail(p, MF_ESTATE, "mf_bank_generate_taylorf2: no bank reserved");
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > p->n_tmpl)
+    return fail(p, MF_EINVAL, "mf_bank_generate_taylorf2: rows out of range");
+  if (!(f_low > 0)) return fail(p, MF_EINVAL, "mf_bank_generate_taylorf2: f_low must be > 0");
+  if (n_rows == 0) return MF_OK;
+  const int64_t ld = (p->nb + 63) / 64 * 64;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_rows, (int64_t(256) << 20) / (ld * 8)));
+  float2* tmp = nullptr;
+  mf_status s = dalloc(p, &tmp, (size_t)chunk * ld * sizeof(float2), "generated rows");
+  if (s != MF_OK) return s;
+  for (int64_t r = 0; r < n_rows && s == MF_OK; r += chunk) {
+    const int64_t cnt = std::min<int64_t>(chunk, n_rows - r);
+    cudaError_t e = mf::launch_taylorf2(m1 + r, m2 + r, cnt, p->d.fs, p->d.n, f_low, tmp, ld, p->st);
+    if (e == cudaErrorInvalidValue) {
+      s = fail(p, MF_EINVAL, "mf_bank_generate_taylorf2: bad masses or band");
+    } else if (e != cudaSuccess) {
+      s = cuda_fail(p, e, "mf_bank_generate_taylorf2");
+    } else {
+      s = p->bank_dtype == MF_F32 ? mf_bank_set_rows(p, row0 + r, cnt, tmp, ld, nullptr, 1)
+                                  : mf_bank_quantize_rows(p, row0 + r, cnt, tmp, ld, 1);
+    }
+  }
+  cudaStreamSynchronize(p->st);
+  cudaFree(tmp);
+  return s;
+}
+
 mf_status mf_set_intermediate(mf_plan_t p, mf_dtype dtype) {
   if (!p) return fail(p, MF_EINVAL, "mf_set_intermediate: null plan");
   if (dtype != MF_F32 && dtype != MF_F16) return fail(p, MF_EINVAL, "mf_set_intermediate: dtype must be F32 or F16");

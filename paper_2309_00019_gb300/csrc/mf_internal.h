@@ -134,6 +134,11 @@ cudaError_t launch_chisq(const void* trig, const int64_t* count, int64_t cap, co
                          int64_t ld_bank, const void* q, int q_type, int64_t ld_q, int n1, int n2, const int32_t* edges,
                          int p, const float* ratio, const float* dscale, float* chi2, float* newsnr, cudaStream_t st);
 
+// TaylorF2 templates (mf_taylorf2.cu): n_tmpl natural-order complex64 rows out [n_tmpl][ld] of an n-sample
+// segment at fs, from host masses; synchronises the stream
+cudaError_t launch_taylorf2(const double* m1, const double* m2, int64_t n_tmpl, double fs, int64_t n, double f_low,
+                            float2* out, int64_t ld, cudaStream_t st);
+
 // blocks x 256 threads, each 8 chains x 16 x iters FP32 FMAs (the ALU probe)
 cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t st);
 

@@ -87,6 +87,8 @@ SIGNATURES = {
     "mf_bank_quantize_rows": (C.c_int, [_P, _I64, _I64, _P, _I64, C.c_int]),
     "mf_set_data_dtype": (C.c_int, [_P, C.c_int]),
     "mf_set_intermediate": (C.c_int, [_P, C.c_int]),
+    "mf_taylorf2": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_int64, C.c_double, _P, C.c_int64, _P]),
+    "mf_bank_generate_taylorf2": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, C.c_double]),
     "mf_set_row_valid": (C.c_int, [_P, _P]),
     "mf_selftest_wait": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mf_chisq": (C.c_int, [_P, C.c_int32, _P, _P]),
@@ -251,6 +253,12 @@ class Plan:
 
     def set_intermediate(self, dtype):
         _check(self.h, self.lib.mf_set_intermediate(self.h, dtype))
+
+    def bank_generate_taylorf2(self, row0, m1, m2, f_low):
+        m1 = np.ascontiguousarray(m1, dtype=np.float64)
+        m2 = np.ascontiguousarray(m2, dtype=np.float64)
+        _check(self.h, self.lib.mf_bank_generate_taylorf2(self.h, row0, len(m1), m1.ctypes.data, m2.ctypes.data,
+                                                          f_low))
 
     def set_row_valid(self, ranges):
         """Per-row analysed ranges, int64 [n_det, 2] (None restores the plan's range)."""
