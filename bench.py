@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "template-seconds filtered/s on 1 GB300 at SNR err<=1e-3; % HBM roofline"
 UNIT = "template-seconds/s"
 WORKLOAD = ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000 @ 512 Hz (N=2^18), "
-            "fine 20000 @ 2048 Hz (N=2^20) on the nbhd union")
+            "fine 20000 @ 2048 Hz (N=2^20) on the union of exact-match (>= 0.9) neighbourhoods")
 FP32_LANES_PER_SM = 128
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
 KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols_h16", "k_rows_tc")}  # k_cols_h16: k_cols with FP16 output
@@ -367,8 +367,13 @@ def main():
 
     cfg = synth.make_config2(seed=segment_seed(1, rank), small=args.small)
     hp = HierParams.from_config(cfg)
-    h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), cfg.nbhd_ptr, cfg.nbhd_idx,
-                  device=dev)
+    if args.small:
+        nb_ptr, nb_idx = cfg.nbhd_ptr, cfg.nbhd_idx
+    else:  # set-up, untimed: neighbourhoods from the exact match >= 0.9, computed with the filter
+        from paper_2309_00019_gb300.nbhd import exact_nbhd_of_config
+        nb_ptr, nb_idx, _ = exact_nbhd_of_config(cfg.coarse_m1, cfg.coarse_m2, cfg.fine_m1, cfg.fine_m2, cfg.f_low,
+                                                 cfg.fs2, device=dev)
+    h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), nb_ptr, nb_idx, device=dev)
     if args.intermediate == "f16":
         h.p2.set_intermediate(mf.MF_F16)
     for r0, rows in synth.taylorf2_chunks_torch(cfg.n1, cfg.fs1, cfg.coarse_m1, cfg.coarse_m2, cfg.f_low, dev,

@@ -33,9 +33,14 @@ def full(lib):
     from paper_2309_00019_gb300.hierarchy import HierParams, Hierarchy
     from paper_2309_00019_gb300.multi import segment_seed
 
+    from paper_2309_00019_gb300.nbhd import exact_nbhd_of_config
+
     c = synth.make_config2(seed=segment_seed(1, 0))  # the bench's segment on rank 0
     hp = HierParams.from_config(c)
     dev = torch.device(DEV)
+    # the bench's neighbourhoods: exact match >= 0.9, computed with the filter (checked in test_gpu_nbhd.py)
+    c.nbhd_ptr, c.nbhd_idx, _ = exact_nbhd_of_config(c.coarse_m1, c.coarse_m2, c.fine_m1, c.fine_m2, c.f_low,
+                                                     c.fs2, device=dev)
     h = Hierarchy(hp, c.psd1, c.psd2, len(c.coarse_m1), len(c.fine_m1), c.nbhd_ptr, c.nbhd_idx, device=dev)
     for r0, rows in synth.taylorf2_chunks_torch(c.n1, c.fs1, c.coarse_m1, c.coarse_m2, c.f_low, dev, chunk=256,
                                                 ld=h.ld1):

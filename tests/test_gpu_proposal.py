@@ -178,3 +178,54 @@ def test_probability_mass_proposal_matches_oracle(mfmod):
         near_tie = len(srt) > 1 and np.abs(np.diff(srt[:9])).min() < 3e-2 * (1 + np.abs(srt[:9]).max())
         assert near_mass or near_tie, (i, got[i], ref[i])
     assert n_same >= 230
+
+
+def test_learned_proposal_on_dense_exact_neighbourhoods(mfmod):
+    """The same learned proposal on neighbourhoods of tens to hundreds of slots:
+    a fine bank six times denser, with neighbourhoods from the exact match
+    (nbhd.exact_nbhd, candidates from the metric map at 0.8)."""
+    from paper_2309_00019_gb300.nbhd import exact_nbhd
+    from paper_2309_00019_gb300.proposal import Proposal, generate_pairs, recovered
+
+    import time
+    rng = np.random.default_rng(21)
+    cm1, cm2, _, _ = synth.sample_bank_chirp_times(rng, 2000, 30.0)
+    fm1, fm2, _, _ = synth.sample_bank_chirp_times(rng, 120000, 30.0)
+    t0 = time.perf_counter()
+    cptr, cidx, _ = synth.nbhd_map(cm1, cm2, fm1, fm2, 30.0, 30.0, 1024.0, min_match=0.8)
+    ptr, idx, _ = exact_nbhd(cm1, cm2, fm1, fm2, 30.0, 2048.0, 1 << 16, cand_ptr=cptr, cand_idx=cidx)
+    t_nb = time.perf_counter() - t0
+    sizes = np.diff(ptr)
+    t0 = time.perf_counter()
+    pairs = generate_pairs(30000 + 1024, cm1, cm2, fm1, fm2, ptr, idx, seed=9)
+    t_gen = time.perf_counter() - t0
+    n_tr = len(pairs.x) - 1024
+    tr = type(pairs)(*(getattr(pairs, f)[:n_tr] for f in ("x", "n_valid", "label", "slot_snr", "coarse")))
+    te = type(pairs)(*(getattr(pairs, f)[n_tr:] for f in ("x", "n_valid", "label", "slot_snr", "coarse")))
+    prop = Proposal(max_batch=1024)
+    prop.init(seed=0)
+    hist = prop.fit(tr, epochs=40, lr=2e-3, batch=1024)
+    assert hist[-1] < hist[0]
+    mean_nb = float(te.n_valid.mean())
+    report = {}
+    for name, k, pm in (("top1", 1, 2.0), ("top4", 4, 2.0), ("top16", 16, 2.0), ("p90", 64, 0.9),
+                        ("p95", 64, 0.95), ("p99", 64, 0.99)):
+        top = prop.rank(te.x, te.n_valid, k, p_mass=pm)
+        frac, used = recovered(te.slot_snr, te.n_valid, top)
+        report[name] = (float(frac.mean()), float(used.mean()))
+    base = {}
+    for k in (4, 16, 64):
+        b = np.array([list(range(min(k, v))) + [-1] * (k - min(k, v)) for v in te.n_valid])
+        bfrac, bused = recovered(te.slot_snr, te.n_valid, b)
+        base[k] = (float(bfrac.mean()), float(bused.mean()))
+    print("\ndense exact neighbourhoods: built in %.0f s (mean %.1f, max %d slots over 2000 coarse templates); "
+          "%d training pairs in %.0f s; 1024 held-out candidates, mean nbhd %.1f"
+          % (t_nb, sizes.mean(), sizes.max(), n_tr, t_gen, mean_nb))
+    print("  (mean recovered SNR fraction, mean templates filtered; the full nbhd: 1.0, %.1f)" % mean_nb)
+    for k, v in report.items():
+        print("  learned", k, tuple(round(x, 4) for x in v))
+    for k, v in base.items():
+        print("  match-order top%d" % k, tuple(round(x, 4) for x in v))
+    assert mean_nb >= 30
+    best = min((v for v in report.values() if v[0] >= 0.99), key=lambda v: v[1], default=None)
+    assert best is not None and best[1] <= 0.9 * mean_nb, (best, mean_nb)
