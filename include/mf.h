@@ -483,7 +483,7 @@ typedef struct {
   float snr, phase;         /* rho and arg z (quantised to 2 pi / 2048) */
 } mf_batch_trigger;
 
-enum { MF_RUN_SERIAL = 0, MF_RUN_STREAMS = 1, MF_RUN_GRAPH = 2 };
+enum { MF_RUN_SERIAL = 0, MF_RUN_STREAMS = 1, MF_RUN_GRAPH = 2, MF_RUN_FUSED = 3, MF_RUN_FUSED_GRAPH = 4 };
 
 mf_status mf_batch_create(mf_batch_t* out, const mf_batch_desc* desc);
 void mf_batch_destroy(mf_batch_t batch);
@@ -505,6 +505,13 @@ mf_status mf_batch_set_segment(mf_batch_t batch, int32_t cls, int64_t n, int32_t
  * series; then as mf_batch_set_segment.  Needs the PSD.  Synchronises. */
 mf_status mf_batch_autotune(mf_batch_t batch, const int64_t* n_tmpl);
 
+/* Autotuner for fused runs (MF_RUN_FUSED): the same probes, but one segment
+ * length N for every class with n_tmpl[c] > 0, the admissible N with the
+ * least summed estimate; each class keeps its own best launch batch at that N
+ * (the fused launch holds the largest of those launches, batch x rows).  Then
+ * as mf_batch_set_segment for each such class.  Synchronises. */
+mf_status mf_batch_autotune_fused(mf_batch_t batch, const int64_t* n_tmpl);
+
 /* Geometry of class c: N_c, L_c, S_c, segments, and the estimated and
  * measured milliseconds per run (measured: of the last MF_RUN_SERIAL run; 0 if none). */
 mf_status mf_batch_segment(mf_batch_t batch, int32_t cls, int64_t* n, int64_t* tmpl_len, int64_t* stride,
@@ -518,7 +525,16 @@ mf_status mf_batch_plan(mf_batch_t batch, int32_t cls, mf_plan_t* plan);
  * other; MF_RUN_STREAMS: each class on its own stream, joined at the end;
  * MF_RUN_GRAPH: as STREAMS, captured once into a CUDA graph per (strain, ld)
  * and replayed (the first run of a batch, or after a bank change, runs
- * uncaptured first).  Asynchronous on the batch's stream. */
+ * uncaptured first).  MF_RUN_FUSED: every class's segment spectra on its own
+ * stream, then one work queue over the (class, template, segment, detector)
+ * series of all classes: each launch pair of the two filter passes takes the
+ * next S series of the queue across class boundaries, S = the largest launch
+ * a class makes alone (its batch x rows); the classes must share N, store an
+ * FP32 bank and use the same intermediate (mf_set_intermediate on every class
+ * plan; MF_ESTATE / MF_EINVAL otherwise).  Triggers are those of the
+ * per-class modes, bit for bit.  A wait that timed out is reported by the
+ * first class with a bank.  MF_RUN_FUSED_GRAPH: FUSED captured and replayed
+ * as GRAPH.  Asynchronous on the batch's stream. */
 mf_status mf_batch_run(mf_batch_t batch, const float* strain, int64_t ld, int32_t mode);
 
 /* Triggers of the last run into host out[cap], ordered by (class, detector,

@@ -1029,3 +1029,119 @@ mf_status mf_nbhd_union(mf_plan_t p, const int32_t* followed, int32_t* subset, i
 }
 
 }  // extern "C"
+
+namespace mf {
+
+int plan_batch(const mf_plan_s* p) { return p ? p->batch : 0; }
+
+int filter_fused(mf_plan_s* const* plans, const void* const* dtilde, const int64_t* ld, int n_plans, void* scratch,
+                 int64_t scratch_series, const CUtensorMap& scratch_map, cudaStream_t st, std::string* err) {
+  auto bad = [&](mf_status s, const std::string& m) {
+    if (err) *err = m;
+    return s;
+  };
+  auto from_plan = [&](mf_plan_s* p, mf_status s) {
+    if (err) *err = p->err;
+    return s;
+  };
+  if (n_plans < 1 || n_plans > kMaxParts || !plans || !dtilde || !ld || !scratch)
+    return bad(MF_EINVAL, "fused filter: bad arguments");
+  mf_plan_s* p0 = plans[0];
+  for (int i = 0; i < n_plans; ++i) {
+    mf_plan_s* p = plans[i];
+    if (!p || !dtilde[i]) return bad(MF_EINVAL, "fused filter: null plan or data");
+    if (!p->psd_set || !p->bank || p->n_tmpl == 0) return bad(MF_ESTATE, "fused filter: a plan has no PSD or bank");
+    if (ld[i] < p->nb) return bad(MF_EINVAL, "fused filter: ld_dtilde < N/2+1");
+    if (p->d.n != p0->d.n || p->bank_dtype != MF_F32 || p->data_dtype != MF_F32 || p->inter_f16 != p0->inter_f16 ||
+        p->d.window != p0->d.window || p->n_win != p0->n_win)
+      return bad(MF_EINVAL, "fused filter: the plans differ in N, window or intermediate, or store 16-bit data");
+    if (p->d.n_det > scratch_series) return bad(MF_EINVAL, "fused filter: scratch smaller than a plan's rows");
+  }
+  const int64_t launches_before = launch_count();
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n_plans; ++i) {
+    mf_plan_s* p = plans[i];
+    mf_status s = ensure_slots(p, p->n_tmpl);
+    if (s != MF_OK) return from_plan(p, s);
+    if (!p->scale_valid) {  // first use: the template scales are written on the plan's own stream
+      if ((s = refresh_scale(p)) != MF_OK) return from_plan(p, s);
+      if ((e = cudaStreamSynchronize(p->st)) != cudaSuccess) return bad(MF_ECUDA, "fused filter: template scales");
+    }
+    e = cudaMemcpyAsync(p->sel_copy, p->sel_all, p->n_tmpl * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_prep_cols(static_cast<const float2*>(dtilde[i]), ld[i], p->w_dev, p->n1, p->n2, p->d.n_det, p->q,
+                           p->ld_q, p->slots, (int64_t)p->d.n_det * p->n_tmpl * p->n_win, st, 1.0 / p->sigma_ref);
+    if (e != cudaSuccess) return bad(MF_ECUDA, std::string("fused filter prep: ") + cudaGetErrorString(e));
+  }
+  FilterArgs a{};
+  a.n = p0->d.n;
+  a.n1 = p0->n1;
+  a.n2 = p0->n2;
+  a.n_det = p0->d.n_det;
+  a.nb = p0->nb;
+  a.bank_type = kBankF32;
+  a.scratch = static_cast<float2*>(scratch);
+  a.window = p0->d.window;
+  a.n_win = p0->n_win;
+  a.status = p0->status;
+  a.tw1 = p0->tw;
+  a.tw2 = p0->tw + 1024;
+  a.tw4 = p0->tw4;
+  a.q_type = kBankF32;
+  a.inter_f16 = p0->inter_f16 ? 1 : 0;
+  // the work queue: (plan, template, row) series in order, cut into launches of at most scratch_series
+  int i = 0;
+  int64_t t = 0;
+  bool first = true;
+  while (i < n_plans) {
+    FilterParts ps{};
+    int64_t ser = 0;
+    while (i < n_plans && ps.n < kMaxParts) {
+      mf_plan_s* p = plans[i];
+      const int64_t rows = p->d.n_det;
+      const int64_t cnt = std::min<int64_t>((scratch_series - ser) / rows, p->n_tmpl - t);
+      if (cnt < 1) break;
+      FilterPart& f = ps.p[ps.n++];
+      f.bank = p->bank;
+      f.ld_bank = p->ld_bank;
+      f.q = p->q;
+      f.ld_q = p->ld_q;
+      f.sel = p->sel_copy;
+      f.inv_sigma = p->ratio_dev;
+      f.thr_raw = p->thr_raw_dev;
+      f.pos0 = t;
+      f.count = (int)cnt;
+      f.n_det = (int)rows;
+      f.valid_begin = p->d.valid_begin;
+      f.valid_end = p->d.valid_end;
+      f.n_sel_total = p->n_tmpl;
+      f.slots = p->slots;
+      f.row_valid = p->row_valid;
+      f.series0 = (int)ser;
+      ser += cnt * rows;
+      t += cnt;
+      if (t == p->n_tmpl) {
+        ++i;
+        t = 0;
+      }
+    }
+    ps.n_series = (int)ser;
+    a.first_batch = first ? 1 : 0;
+    first = false;
+    if ((e = launch_filter2_fused(a, ps, scratch_map, st)) != cudaSuccess)
+      return bad(MF_ECUDA, std::string("fused filter launch: ") + cudaGetErrorString(e));
+  }
+  for (int j = 0; j < n_plans; ++j) {
+    mf_plan_s* p = plans[j];
+    e = launch_compact(p->slots, p->d.n_det, p->n_tmpl, p->n_win, p->d.window, p->sel_copy, p->trig,
+                       p->d.max_triggers, p->count, p->bc, p->bc_cap, st);
+    if (e != cudaSuccess) return bad(MF_ECUDA, std::string("fused filter compaction: ") + cudaGetErrorString(e));
+    p->n_sel = p->n_tmpl;
+    p->filtered = true;
+    p->coinc_done = false;
+  }
+  p0->stats.launches += launch_count() - launches_before;
+  return MF_OK;
+}
+
+}  // namespace mf

@@ -73,8 +73,13 @@ struct mf_batch_s {
     float2* fd = nullptr;
   };
   std::vector<Cls> cls;
-  // captured graph of one MF_RUN_STREAMS pass
+  // fused runs: the scratch of one launch pair (fscratch_series series of N = fscratch_n) and its pass-2 map
+  float2* fscratch = nullptr;
+  int64_t fscratch_series = 0, fscratch_n = 0;
+  CUtensorMap fmap{};
+  // captured graph of one MF_RUN_STREAMS (or MF_RUN_FUSED) pass
   cudaGraphExec_t exec = nullptr;
+  int32_t g_mode = -1;
   const float* g_strain = nullptr;
   int64_t g_ld = 0;
   std::vector<uint64_t> g_fp;
@@ -155,7 +160,83 @@ mf_status make_plan(mf_batch_s* b, int64_t n, int64_t rows, int64_t vb, int64_t 
   return MF_OK;
 }
 
+mf_status enqueue_spectra(mf_batch_s* b, mf_batch_s::Cls& c, const float* strain, int64_t ld);
+
 mf_status enqueue_class(mf_batch_s* b, mf_batch_s::Cls& c, const float* strain, int64_t ld) {
+  mf_status s = enqueue_spectra(b, c, strain, ld);
+  if (s != MF_OK) return s;
+  s = mf_filter(c.plan, c.fd, c.ld, nullptr, -1);
+  if (s != MF_OK) return bplan(b, c.plan, s, "class filter");
+  return MF_OK;
+}
+
+bool has_bank(const mf_batch_s::Cls& c) { return c.plan && mf::plan_templates(c.plan) > 0; }
+
+struct Probe {  // the autotuner's timing events
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Probe() {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  ~Probe() {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+};
+
+// Time class ci at segment length n: 2 filter calls of a zero probe bank on the class's real row
+// count for each of 3 launch batches (the largest fitting 128 MB, 256 MB and 1 GB of
+// intermediate).  *ms = the least n_tmpl x time per template (+inf if n is inadmissible), *batch its batch.
+mf_status probe_class(mf_batch_t b, int ci, int64_t n, int64_t n_tmpl, Probe& pr, double* ms_out, int32_t* batch) {
+  *ms_out = INFINITY;
+  int64_t L, stride, n_seg;
+  if (!geometry(b, ci, n, &L, &stride, &n_seg)) return MF_OK;
+  const int64_t rows = n_seg * b->d.n_det;
+  const int64_t per = rows * n * (int64_t)sizeof(float2);
+  std::vector<int32_t> cands;
+  for (int64_t budget : {int64_t(128) << 20, int64_t(256) << 20, int64_t(1) << 30}) {
+    const int32_t bb = (int32_t)std::max<int64_t>(1, std::min<int64_t>({budget / per, n_tmpl, 256}));
+    if (std::find(cands.begin(), cands.end(), bb) == cands.end()) cands.push_back(bb);
+  }
+  const int32_t probe = std::max<int32_t>(8, std::min<int32_t>(64, 2 * *std::max_element(cands.begin(), cands.end())));
+  mf_plan_t p = nullptr;
+  mf_status s = make_plan(b, n, rows, L, 1024, b->main, &p);
+  if (s != MF_OK) return s;
+  float2* fd = nullptr;
+  const int64_t ld = (n / 2 + 1 + 63) / 64 * 64;
+  cudaError_t ce = cudaMalloc((void**)&fd, (size_t)rows * ld * sizeof(float2));
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(fd, 0, (size_t)rows * ld * sizeof(float2), b->main);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    if (fd) cudaFree(fd);
+    mf_destroy(p);
+    return bfail(b, MF_ENOMEM, "mf_batch_autotune probe data");
+  }
+  s = mf_bank_reserve(p, MF_F32, probe);
+  for (int32_t bb : cands) {
+    if (s == MF_OK) s = mf_set_batch(p, bb);
+    if (s == MF_OK) s = mf_filter(p, fd, ld, nullptr, -1);  // warm-up (tables, tensor maps)
+    if (s != MF_OK) break;
+    cudaEventRecord(pr.e0, b->main);
+    for (int it = 0; it < 2 && s == MF_OK; ++it) s = mf_filter(p, fd, ld, nullptr, -1);
+    cudaEventRecord(pr.e1, b->main);
+    if (cudaEventSynchronize(pr.e1) != cudaSuccess || s != MF_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pr.e0, pr.e1);
+    const double est = (double)ms / (2.0 * probe) * (double)n_tmpl;
+    if (est < *ms_out) {
+      *ms_out = est;
+      *batch = bb;
+    }
+  }
+  if (s != MF_OK) s = bplan(b, p, s, "mf_batch_autotune probe");
+  cudaFree(fd);
+  mf_destroy(p);
+  return s;
+}
+
+// spectra of class c's segment rows: gather from the stream, then the plan's real-input transform
+mf_status enqueue_spectra(mf_batch_s* b, mf_batch_s::Cls& c, const float* strain, int64_t ld) {
   const int64_t total = c.rows * c.n;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count_b() * 8);
   k_segments<<<grid, 256, 0, c.st>>>(strain, ld, b->d.n_det, b->d.n_samples, c.stride, ilog2(c.n), c.rows, c.seg);
@@ -164,12 +245,70 @@ mf_status enqueue_class(mf_batch_s* b, mf_batch_s::Cls& c, const float* strain, 
   if (e != cudaSuccess) return bcuda(b, e, "segment gather");
   mf_status s = mf_strain_to_fd(c.plan, c.seg, c.n, c.fd, c.ld);
   if (s != MF_OK) return bplan(b, c.plan, s, "segment spectra");
-  s = mf_filter(c.plan, c.fd, c.ld, nullptr, -1);
-  if (s != MF_OK) return bplan(b, c.plan, s, "class filter");
   return MF_OK;
 }
 
-bool has_bank(const mf_batch_s::Cls& c) { return c.plan && mf::plan_templates(c.plan) > 0; }
+// series per fused launch: the largest launch pair a class makes on its own (its batch x rows)
+int64_t fused_series(const mf_batch_s* b) {
+  int64_t n = 0;
+  for (const auto& c : b->cls)
+    if (has_bank(c)) n = std::max<int64_t>(n, (int64_t)mf::plan_batch(c.plan) * c.rows);
+  return n;
+}
+
+// the fused run's scratch (and its pass-2 map) for the classes' common segment length
+mf_status ensure_fused(mf_batch_s* b) {
+  int64_t n = 0;
+  for (const auto& c : b->cls) {
+    if (!has_bank(c)) continue;
+    if (n != 0 && c.n != n)
+      return bfail(b, MF_ESTATE, "mf_batch_run: a fused run needs one segment length for every class with a bank");
+    n = c.n;
+  }
+  const int64_t series = fused_series(b);
+  if (b->fscratch && b->fscratch_n == n && b->fscratch_series == series) return MF_OK;
+  cudaStreamSynchronize(b->main);  // the old scratch may still be read
+  if (b->fscratch) cudaFree(b->fscratch);
+  b->fscratch = nullptr;
+  b->fscratch_series = 0;
+  cudaError_t e = cudaMalloc((void**)&b->fscratch, (size_t)series * n * sizeof(float2));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->fscratch = nullptr;
+    return bfail(b, MF_ENOMEM, std::string("mf_batch_run fused scratch: ") + cudaGetErrorString(e));
+  }
+  e = mf::encode_scratch_map(n, b->fscratch, series, &b->fmap);
+  if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run fused scratch map");
+  b->fscratch_n = n;
+  b->fscratch_series = series;
+  return MF_OK;
+}
+
+// one fused pass: every class's spectra on its own stream, then the classes' work queue on the main stream
+mf_status enqueue_fused(mf_batch_s* b, const float* strain, int64_t ld) {
+  cudaError_t e = cudaEventRecord(b->ev_in, b->main);
+  std::vector<mf_plan_t> plans;
+  std::vector<const void*> fd;
+  std::vector<int64_t> lds;
+  for (auto& c : b->cls) {
+    if (!has_bank(c) || e != cudaSuccess) continue;
+    e = cudaStreamWaitEvent(c.st, b->ev_in, 0);
+    if (e != cudaSuccess) break;
+    mf_status s = enqueue_spectra(b, c, strain, ld);
+    if (s != MF_OK) return s;
+    e = cudaEventRecord(c.join, c.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, c.join, 0);
+    plans.push_back(c.plan);
+    fd.push_back(c.fd);
+    lds.push_back(c.ld);
+  }
+  if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run fused order");
+  std::string m;
+  const int s = mf::filter_fused(plans.data(), fd.data(), lds.data(), (int)plans.size(), b->fscratch,
+                                 b->fscratch_series, b->fmap, b->main, &m);
+  if (s != MF_OK) return bfail(b, (mf_status)s, m);
+  return MF_OK;
+}
 
 }  // namespace
 
@@ -222,6 +361,7 @@ void mf_batch_destroy(mf_batch_t b) {
     if (c.t1) cudaEventDestroy(c.t1);
     if (c.join) cudaEventDestroy(c.join);
   }
+  if (b->fscratch) cudaFree(b->fscratch);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->main) cudaStreamDestroy(b->main);
@@ -291,64 +431,22 @@ mf_status mf_batch_set_segment(mf_batch_t b, int32_t ci, int64_t n, int32_t per_
 mf_status mf_batch_autotune(mf_batch_t b, const int64_t* n_tmpl) {
   if (!b || !n_tmpl) return bfail(b, MF_EINVAL, "mf_batch_autotune: null argument");
   if (b->n_psd == 0) return bfail(b, MF_ESTATE, "mf_batch_autotune: PSD not set");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  Probe pr;
   mf_status result = MF_OK;
   for (int ci = 0; ci < b->d.n_class && result == MF_OK; ++ci) {
     if (n_tmpl[ci] <= 0) continue;
     double best = INFINITY;
     int64_t best_n = 0;
     int32_t best_b = 0;
-    for (int64_t n = 4096; n <= std::min<int64_t>(mf::kMaxN, b->n_psd); n *= 2) {
-      int64_t L, stride, n_seg;
-      if (!geometry(b, ci, n, &L, &stride, &n_seg)) continue;
-      const int64_t rows = n_seg * b->d.n_det;
-      const int64_t per = rows * n * (int64_t)sizeof(float2);
-      // launch batches: the largest that fit 128 MB, 256 MB and 1 GB of intermediate (at least 1)
-      std::vector<int32_t> cands;
-      for (int64_t budget : {int64_t(128) << 20, int64_t(256) << 20, int64_t(1) << 30}) {
-        const int32_t bb = (int32_t)std::max<int64_t>(1, std::min<int64_t>({budget / per, n_tmpl[ci], 256}));
-        if (std::find(cands.begin(), cands.end(), bb) == cands.end()) cands.push_back(bb);
+    for (int64_t n = 4096; n <= std::min<int64_t>(mf::kMaxN, b->n_psd) && result == MF_OK; n *= 2) {
+      double ms = INFINITY;
+      int32_t bb = 0;
+      result = probe_class(b, ci, n, n_tmpl[ci], pr, &ms, &bb);
+      if (ms < best) {
+        best = ms;
+        best_n = n;
+        best_b = bb;
       }
-      const int32_t probe = std::max<int32_t>(8, std::min<int32_t>(64, 2 * *std::max_element(cands.begin(), cands.end())));
-      mf_plan_t p = nullptr;
-      mf_status s = make_plan(b, n, rows, L, 1024, b->main, &p);
-      if (s != MF_OK) {
-        result = s;
-        break;
-      }
-      float2* fd = nullptr;
-      const int64_t ld = (n / 2 + 1 + 63) / 64 * 64;
-      cudaError_t ce = cudaMalloc((void**)&fd, (size_t)rows * ld * sizeof(float2));
-      if (ce == cudaSuccess) ce = cudaMemsetAsync(fd, 0, (size_t)rows * ld * sizeof(float2), b->main);
-      if (ce != cudaSuccess) {
-        cudaGetLastError();
-        mf_destroy(p);
-        result = bfail(b, MF_ENOMEM, "mf_batch_autotune probe data");
-        break;
-      }
-      s = mf_bank_reserve(p, MF_F32, probe);
-      for (int32_t bb : cands) {
-        if (s == MF_OK) s = mf_set_batch(p, bb);
-        if (s == MF_OK) s = mf_filter(p, fd, ld, nullptr, -1);  // warm-up (tables, tensor maps)
-        if (s != MF_OK) break;
-        cudaEventRecord(e0, b->main);
-        for (int it = 0; it < 2 && s == MF_OK; ++it) s = mf_filter(p, fd, ld, nullptr, -1);
-        cudaEventRecord(e1, b->main);
-        if (cudaEventSynchronize(e1) != cudaSuccess || s != MF_OK) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double est = (double)ms / (2.0 * probe) * (double)n_tmpl[ci];
-        if (est < best) {
-          best = est;
-          best_n = n;
-          best_b = bb;
-        }
-      }
-      if (s != MF_OK) result = bplan(b, p, s, "mf_batch_autotune probe");
-      cudaFree(fd);
-      mf_destroy(p);
     }
     if (result != MF_OK) break;
     if (best_n == 0) {
@@ -358,9 +456,50 @@ mf_status mf_batch_autotune(mf_batch_t b, const int64_t* n_tmpl) {
     result = mf_batch_set_segment(b, ci, best_n, best_b);
     if (result == MF_OK) b->cls[ci].est_ms = best;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return result;
+}
+
+mf_status mf_batch_autotune_fused(mf_batch_t b, const int64_t* n_tmpl) {
+  if (!b || !n_tmpl) return bfail(b, MF_EINVAL, "mf_batch_autotune_fused: null argument");
+  if (b->n_psd == 0) return bfail(b, MF_ESTATE, "mf_batch_autotune_fused: PSD not set");
+  Probe pr;
+  const int nc = b->d.n_class;
+  double best = INFINITY;
+  int64_t best_n = 0;
+  std::vector<double> best_ms(nc, 0.0), ms(nc, 0.0);
+  std::vector<int32_t> best_b(nc, 0), bb(nc, 0);
+  for (int64_t n = 4096; n <= std::min<int64_t>(mf::kMaxN, b->n_psd); n *= 2) {
+    bool fits = true;  // probe only lengths that every class with templates admits
+    for (int ci = 0; ci < nc; ++ci) {
+      int64_t L, stride, n_seg;
+      if (n_tmpl[ci] > 0 && !geometry(b, ci, n, &L, &stride, &n_seg)) fits = false;
+    }
+    if (!fits) continue;
+    double total = 0.0;
+    bool any = false;
+    for (int ci = 0; ci < nc && std::isfinite(total); ++ci) {
+      if (n_tmpl[ci] <= 0) continue;
+      ms[ci] = INFINITY;
+      mf_status s = probe_class(b, ci, n, n_tmpl[ci], pr, &ms[ci], &bb[ci]);
+      if (s != MF_OK) return s;
+      total += ms[ci];  // +inf when the class does not fit segments of n
+      any = true;
+    }
+    if (any && total < best) {
+      best = total;
+      best_n = n;
+      best_ms = ms;
+      best_b = bb;
+    }
+  }
+  if (best_n == 0) return bfail(b, MF_EINVAL, "mf_batch_autotune_fused: no segment length admissible for every class");
+  for (int ci = 0; ci < nc; ++ci) {
+    if (n_tmpl[ci] <= 0) continue;
+    mf_status s = mf_batch_set_segment(b, ci, best_n, best_b[ci]);
+    if (s != MF_OK) return s;
+    b->cls[ci].est_ms = best_ms[ci];
+  }
+  return MF_OK;
 }
 
 mf_status mf_batch_segment(mf_batch_t b, int32_t ci, int64_t* n, int64_t* tmpl_len, int64_t* stride, int64_t* n_seg,
@@ -390,42 +529,54 @@ mf_status mf_batch_plan(mf_batch_t b, int32_t ci, mf_plan_t* plan) {
 mf_status mf_batch_run(mf_batch_t b, const float* strain, int64_t ld, int32_t mode) {
   if (!b || !strain) return bfail(b, MF_EINVAL, "mf_batch_run: null argument");
   if (ld < b->d.n_samples) return bfail(b, MF_EINVAL, "mf_batch_run: ld < n_samples");
-  if (mode < MF_RUN_SERIAL || mode > MF_RUN_GRAPH) return bfail(b, MF_EINVAL, "mf_batch_run: mode");
+  if (mode < MF_RUN_SERIAL || mode > MF_RUN_FUSED_GRAPH) return bfail(b, MF_EINVAL, "mf_batch_run: mode");
   bool any = false;
   for (auto& c : b->cls) any |= has_bank(c);
   if (!any) return bfail(b, MF_ESTATE, "mf_batch_run: no class has a bank");
+  const bool fused = mode == MF_RUN_FUSED || mode == MF_RUN_FUSED_GRAPH;
+  mf_status s = MF_OK;
+  if (fused && (s = ensure_fused(b)) != MF_OK) return s;
   cudaError_t e = cudaEventRecord(b->ev_in, b->user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->ev_in, 0);
   if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run order");
-  mf_status s = MF_OK;
-  if (mode == MF_RUN_GRAPH) {
-    std::vector<uint64_t> fp;
+  if (mode == MF_RUN_GRAPH || mode == MF_RUN_FUSED_GRAPH) {
+    auto fingerprint = [&]() {
+      std::vector<uint64_t> fp;
+      for (auto& c : b->cls) fp.push_back(has_bank(c) ? mf::plan_fingerprint(c.plan) : 0);
+      if (fused) {
+        fp.push_back((uint64_t)(uintptr_t)b->fscratch);
+        fp.push_back((uint64_t)b->fscratch_series);
+      }
+      return fp;
+    };
+    std::vector<uint64_t> fp = fingerprint();
     bool ready = b->ran;
-    for (auto& c : b->cls) {
-      fp.push_back(has_bank(c) ? mf::plan_fingerprint(c.plan) : 0);
+    for (auto& c : b->cls)
       if (has_bank(c)) ready = ready && mf::plan_capturable(c.plan);
-    }
     if (!ready) {  // one uncaptured pass does every first-call set-up (host syncs, allocations)
-      s = mf_batch_run(b, strain, ld, MF_RUN_STREAMS);
+      s = mf_batch_run(b, strain, ld, fused ? MF_RUN_FUSED : MF_RUN_STREAMS);
       if (s != MF_OK) return s;
       cudaStreamSynchronize(b->main);
-      fp.clear();
-      for (auto& c : b->cls) fp.push_back(has_bank(c) ? mf::plan_fingerprint(c.plan) : 0);
+      fp = fingerprint();
     }
-    if (!b->exec || b->g_strain != strain || b->g_ld != ld || b->g_fp != fp) {
+    if (!b->exec || b->g_mode != mode || b->g_strain != strain || b->g_ld != ld || b->g_fp != fp) {
       if (b->exec) cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run capture");
-      cudaEvent_t fork = b->ev_in;
-      e = cudaEventRecord(fork, b->main);
-      for (auto& c : b->cls) {
-        if (!has_bank(c) || e != cudaSuccess || s != MF_OK) continue;
-        e = cudaStreamWaitEvent(c.st, fork, 0);
-        if (e == cudaSuccess) s = enqueue_class(b, c, strain, ld);
-        if (e == cudaSuccess && s == MF_OK) e = cudaEventRecord(c.join, c.st);
-        if (e == cudaSuccess && s == MF_OK) e = cudaStreamWaitEvent(b->main, c.join, 0);
+      if (fused) {
+        s = enqueue_fused(b, strain, ld);
+      } else {
+        cudaEvent_t fork = b->ev_in;
+        e = cudaEventRecord(fork, b->main);
+        for (auto& c : b->cls) {
+          if (!has_bank(c) || e != cudaSuccess || s != MF_OK) continue;
+          e = cudaStreamWaitEvent(c.st, fork, 0);
+          if (e == cudaSuccess) s = enqueue_class(b, c, strain, ld);
+          if (e == cudaSuccess && s == MF_OK) e = cudaEventRecord(c.join, c.st);
+          if (e == cudaSuccess && s == MF_OK) e = cudaStreamWaitEvent(b->main, c.join, 0);
+        }
       }
       cudaError_t e2 = cudaStreamEndCapture(b->main, &g);
       if (s != MF_OK) {
@@ -436,12 +587,15 @@ mf_status mf_batch_run(mf_batch_t b, const float* strain, int64_t ld, int32_t mo
       if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
       if (g) cudaGraphDestroy(g);
       if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run graph");
+      b->g_mode = mode;
       b->g_strain = strain;
       b->g_ld = ld;
       b->g_fp = fp;
     }
     e = cudaGraphLaunch(b->exec, b->main);
     if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run graph launch");
+  } else if (mode == MF_RUN_FUSED) {
+    if ((s = enqueue_fused(b, strain, ld)) != MF_OK) return s;
   } else {
     cudaEvent_t prev = b->ev_in;
     e = cudaEventRecord(prev, b->main);
@@ -463,6 +617,9 @@ mf_status mf_batch_run(mf_batch_t b, const float* strain, int64_t ld, int32_t mo
   }
   e = cudaEventRecord(b->ev_out, b->main);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->ev_out, 0);
+  // a fused pass filtered on the main stream: later calls on a class's plan (its own stream) follow it
+  for (auto& c : b->cls)
+    if (fused && has_bank(c) && e == cudaSuccess) e = cudaStreamWaitEvent(c.st, b->ev_out, 0);
   if (e != cudaSuccess) return bcuda(b, e, "mf_batch_run join");
   b->ran = true;
   return MF_OK;

@@ -182,8 +182,10 @@ __global__ void k_fill_twiddles(float2* tw) {
 // rows that are the tensor-core row pass's stage-1 operand image: with k2 = 32 p + q, part c (0 real,
 // 1 imaginary) of element (j1, k2) is the half at panel j1 / 8, ((q 32 + p) 2 + c) 8 + j1 % 8 (panels of
 // 2 N2 8 halves), i.e. the MN-major layout of rows m = 8 q + j1 % 8 and columns k = 2 p + c
-template <int N1, int N2, int BT, int QT, bool H16>
-__global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
+// MP: the series of several plans' parts (FilterParts), each with its own bank, data rows and selection
+template <int N1, int N2, int BT, int QT, bool H16, bool MP>
+__global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a, const __grid_constant__ FilterParts ps) {
+  static_assert(!MP || QT == kBankF32, "fused launches take FP32 weighted data");
   using G = SubFft<N1>;
   using P = ColGeo<N1, BT, QT>;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
   uint64_t* empty = full + 2;                                     // [0], [1]: every warp done with the slot
   uint64_t* twb = full + 4;                                       // the twiddle table landed
   const int tid = threadIdx.x;
-  const int n_items = a.count * a.n_det * NCB;
+  const int n_items = (MP ? ps.n_series : a.count * a.n_det) * NCB;
   if (tid == 0) {
     mbar_init(full + 0, 1);
     mbar_init(full + 1, 1);
@@ -224,19 +226,33 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
         const int slot = k & 1;
         if (k >= 2 && !(ok = mbar_wait_bounded(empty + slot, (uint32_t)(((k >> 1) + 1) & 1), a.status))) break;
         fence_proxy_async();
+        int li = item, nd = a.n_det;
+        const int32_t* sel = a.sel;
+        int64_t pos0 = a.pos0, ld_bank = a.ld_bank, ld_q = a.ld_q;
+        const unsigned char *hb = static_cast<const unsigned char*>(a.bank), *qb = qbase;
+        if constexpr (MP) {
+          const FilterPart& p = ps.p[part_of(ps, item, NCB)];
+          li = item - p.series0 * NCB;
+          nd = p.n_det;
+          sel = p.sel;
+          pos0 = p.pos0;
+          hb = static_cast<const unsigned char*>(p.bank);
+          ld_bank = p.ld_bank;
+          qb = reinterpret_cast<const unsigned char*>(p.q);
+          ld_q = p.ld_q;
+        }
         // detector fastest: the n_det items of one bank tile are issued back to back, so the
         // tile is read from HBM once and from L2 for the other detectors
-        const int d = item % a.n_det, cb = (item / a.n_det) % NCB, b = item / (a.n_det * NCB);
-        const int64_t tmpl = a.sel[a.pos0 + b];
+        const int d = li % nd, cb = (li / nd) % NCB, b = li / (nd * NCB);
+        const int64_t tmpl = sel[pos0 + b];
         unsigned char* dst = sm + slot * P::SLOT;
         mbar_expect_tx(full + slot, (uint32_t)(C * (P::H_COL + P::Q_COL)));
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const int64_t col = (int64_t)cb * C + c;
           // default L2 priority: the n_det - 1 later items of this tile read it from L2
-          bulk_g2s(dst + c * S * 8, static_cast<const unsigned char*>(a.bank) + (tmpl * a.ld_bank + col * R) * P::HB,
-                   (uint32_t)P::H_COL, full + slot);
-          bulk_g2s(dst + c * S * 8 + P::H_COL, qbase + ((int64_t)d * a.ld_q + col * R) * P::QB, (uint32_t)P::Q_COL,
+          bulk_g2s(dst + c * S * 8, hb + (tmpl * ld_bank + col * R) * P::HB, (uint32_t)P::H_COL, full + slot);
+          bulk_g2s(dst + c * S * 8 + P::H_COL, qb + ((int64_t)d * ld_q + col * R) * P::QB, (uint32_t)P::Q_COL,
                    full + slot);
         }
       }
@@ -264,7 +280,20 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     const int slot = k & 1;
     if (!mbar_wait_bounded(full + slot, (uint32_t)((k >> 1) & 1), a.status)) break;
     const unsigned char* col = sm + slot * P::SLOT + ca * S * 8;
-    const int s = (item / (a.n_det * NCB)) * a.n_det + item % a.n_det;
+    int li = item, nd = a.n_det, s0 = 0;
+    const int32_t* sel = a.sel;
+    const float* isg = a.inv_sigma;
+    int64_t pos0 = a.pos0;
+    if constexpr (MP) {
+      const FilterPart& p = ps.p[part_of(ps, item, NCB)];
+      li = item - p.series0 * NCB;
+      nd = p.n_det;
+      s0 = p.series0;
+      sel = p.sel;
+      isg = p.inv_sigma;
+      pos0 = p.pos0;
+    }
+    const int s = s0 + (li / (nd * NCB)) * nd + li % nd;
     float2 v[RA];
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
@@ -283,9 +312,9 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
     __syncwarp();
     float2* out = a.scratch + (int64_t)s * N;
     __half* out16 = reinterpret_cast<__half*>(a.scratch) + (int64_t)s * 2 * N;
-    const int k2 = ((item / a.n_det) % NCB) * C + ca;
+    const int k2 = ((li / nd) % NCB) * C + ca;
     float sc = 1.f;
-    if constexpr (H16) sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + item / (a.n_det * NCB)]));
+    if constexpr (H16) sc = series_scale16(__ldg(isg + sel[pos0 + li / (nd * NCB)]));
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = ta + T * i;
@@ -349,8 +378,10 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a) {
 
 // tm: the scratch as [series * N1 / PH panels][N2][PH] of 8-byte values, box
 // {RW, BOXY, 1} (unused when RW = PH: an item is then one contiguous panel)
-template <int N1, int N2>
-__global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtensorMap tm, FilterArgs a) {
+// MP: the series of several plans' parts (FilterParts), each with its own epilogue state
+template <int N1, int N2, bool MP>
+__global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtensorMap tm, FilterArgs a,
+                                                 const __grid_constant__ FilterParts ps) {
   using G = SubFft<N2>;
   using P = RowGeo<N2>;
   using X = typename P::X;
@@ -364,7 +395,7 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
   const int tid = threadIdx.x;
   const int row = tid % RW, t = tid / RW;  // rows fastest: the panel is [k2][row]
   // series in reverse order: the last ones pass 1 wrote are the likeliest to be still in L2
-  const int n_series = a.count * a.n_det;
+  const int n_series = MP ? ps.n_series : a.count * a.n_det;
   const int n_items = n_series * NRB;
   if (tid == 0) {
     mbar_init(bar + 0, 1);
@@ -429,7 +460,15 @@ __global__ void __launch_bounds__(kT2, 3) k_rows(const __grid_constant__ CUtenso
 #pragma unroll
     for (int q = 0; q < RA; ++q) xb[X::idx(row, t * RA + q)] = v[q];
     __syncthreads();
-    const auto se = ep.series(s);
+    RawEpi::Ser se;
+    if constexpr (MP) {
+      const FilterPart& p = ps.p[part_of(ps, s, 1)];
+      const RawEpi pe{p.sel,           p.inv_sigma, p.thr_raw,     nullptr, p.pos0,   p.n_det,      a.window,
+                      p.valid_begin,   p.valid_end, a.n_win,       p.n_sel_total,     p.slots,      p.row_valid};
+      se = pe.series(s - p.series0);
+    } else {
+      se = ep.series(s);
+    }
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = t + T * i;
@@ -482,69 +521,83 @@ int grid2(int items) {
   return items < g ? items : g;
 }
 
-template <int N1, int N2, int BT, int QT, bool H16 = false>
-cudaError_t run_cols(const FilterArgs& a, cudaStream_t st) {
+template <int N1, int N2, int BT, int QT, bool H16 = false, bool MP = false>
+cudaError_t run_cols(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
   using P = ColGeo<N1, BT, QT>;
   static_assert(P::SMEM * 3 <= 230400, "k_cols: three CTAs per SM must fit in shared memory");
-  auto k = k_cols<N1, N2, BT, QT, H16>;
+  auto k = k_cols<N1, N2, BT, QT, H16, MP>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem2(k, P::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int items = a.count * a.n_det * (N2 / P::C);
-  cudaError_t e = launch_pdl(k, grid2(items), kColThreads, P::SMEM, st, a);
+  const int items = (MP ? ps.n_series : a.count * a.n_det) * (N2 / P::C);
+  cudaError_t e = launch_pdl(k, grid2(items), kColThreads, P::SMEM, st, a, ps);
   add_launches(1);
   return e;
 }
 
-// (bank, data) storage pairs: FP32 data with any bank; 16-bit data with a bank of the same type
+// (bank, data) storage pairs: FP32 data with any bank; 16-bit data with a bank of the same type.
+// Fused launches (ps.n > 0): FP32 data, an FP32 bank.
 template <int N1, int N2>
-cudaError_t run_cols_bt(const FilterArgs& a, cudaStream_t st) {
+cudaError_t run_cols_bt(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
+  const bool mp = ps.n > 0;
+  if (mp && (a.q_type != kBankF32 || a.bank_type != kBankF32)) return cudaErrorInvalidValue;
   if constexpr (N1 == 1024 && N2 == 1024) {
     if (a.inter_f16) {  // FP16 intermediate for the tensor-core row pass: FP32 data, any bank
       if (a.q_type != kBankF32) return cudaErrorInvalidValue;
+      if (mp) return run_cols<N1, N2, kBankF32, kBankF32, true, true>(a, ps, st);
       switch (a.bank_type) {
-        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, true>(a, st);
-        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, true>(a, st);
-        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, true>(a, st);
+        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, true>(a, ps, st);
+        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, true>(a, ps, st);
+        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, true>(a, ps, st);
       }
       return cudaErrorInvalidValue;
     }
   } else {
     if (a.inter_f16) return cudaErrorInvalidValue;
   }
+  if (mp) return run_cols<N1, N2, kBankF32, kBankF32, false, true>(a, ps, st);
   if (a.q_type == kBankF32) {
     switch (a.bank_type) {
-      case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32>(a, st);
-      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32>(a, st);
-      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32>(a, st);
+      case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32>(a, ps, st);
+      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32>(a, ps, st);
+      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32>(a, ps, st);
     }
   } else if (a.q_type == a.bank_type) {
     switch (a.bank_type) {
-      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF16>(a, st);
-      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankBF16>(a, st);
+      case kBankF16: return run_cols<N1, N2, kBankF16, kBankF16>(a, ps, st);
+      case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankBF16>(a, ps, st);
     }
   }
   return cudaErrorInvalidValue;
 }
 
-template <int N1, int N2>
-cudaError_t run_rows(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
+template <int N1, int N2, bool MP>
+cudaError_t run_rows_mp(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
   using P = RowGeo<N2>;
   static_assert(P::SMEM * 3 <= 230400, "k_rows: three CTAs per SM must fit in shared memory");
-  auto k = k_rows<N1, N2>;
+  auto k = k_rows<N1, N2, MP>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem2(k, P::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int items = a.count * a.n_det * (N1 / P::RW);
-  cudaError_t e = launch_pdl(k, grid2(items), kT2, P::SMEM, st, tm, a);
+  const int items = (MP ? ps.n_series : a.count * a.n_det) * (N1 / P::RW);
+  cudaError_t e = launch_pdl(k, grid2(items), kT2, P::SMEM, st, tm, a, ps);
   add_launches(1);
   return e;
+}
+
+template <int N1, int N2>
+cudaError_t run_rows(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
+  if (ps.n > 0) {
+    if (a.q_type != kBankF32) return cudaErrorInvalidValue;
+    return run_rows_mp<N1, N2, true>(a, ps, tm, st);
+  }
+  return run_rows_mp<N1, N2, false>(a, ps, tm, st);
 }
 
 // signature of the driver's cuTensorMapEncodeTiled (CUDA 12.0 ABI), fetched at run time
@@ -627,11 +680,32 @@ cudaError_t tw4_count_of(int64_t* c) {
 
 }  // namespace
 
-cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { MF_DISPATCH2(a.n, run_cols_bt, (a, st)) }
+namespace {
+
+const FilterParts kOnePlan{};  // n = 0: every per-series field from FilterArgs
+
+cudaError_t pass1_parts(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
+  MF_DISPATCH2(a.n, run_cols_bt, (a, ps, st))
+}
+
+cudaError_t pass2_parts(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
+  if (a.inter_f16) return launch_filter2_pass2_tc(a, st, ps.n > 0 ? &ps : nullptr);
+  MF_DISPATCH2(a.n, run_rows, (a, ps, tm, st))
+}
+
+}  // namespace
+
+cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st) { return pass1_parts(a, kOnePlan, st); }
 
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& tm, cudaStream_t st) {
-  if (a.inter_f16) return launch_filter2_pass2_tc(a, st);
-  MF_DISPATCH2(a.n, run_rows, (a, tm, st))
+  return pass2_parts(a, kOnePlan, tm, st);
+}
+
+cudaError_t launch_filter2_fused(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
+  if (ps.n < 1 || ps.n > kMaxParts || ps.n_series < 1) return cudaErrorInvalidValue;
+  cudaError_t e = pass1_parts(a, ps, st);
+  if (e == cudaSuccess) e = pass2_parts(a, ps, tm, st);
+  return e;
 }
 
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m) {

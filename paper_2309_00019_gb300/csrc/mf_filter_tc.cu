@@ -84,8 +84,9 @@ __device__ __forceinline__ void stage_mmas(uint32_t d, uint32_t a_addr, bool mn_
 // parity of the n-th completion (n = 0, 1, ...) of a barrier
 __device__ __forceinline__ uint32_t par(int n) { return (uint32_t)(n & 1); }
 
-template <int N1>
-__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
+// MP: the series of several plans' parts (FilterParts), each with its own epilogue state
+template <int N1, bool MP>
+__global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const __grid_constant__ FilterParts ps) {
   constexpr int N2 = 1024;
   constexpr int64_t N = (int64_t)N1 * N2;
   constexpr int NP = N1 / kTcRows;  // panels (items) per series
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
   uint64_t* drain = tfree + kGroups;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBAR_OFF + kNBar * 8);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
-  const int n_series = a.count * a.n_det;
+  const int n_series = MP ? ps.n_series : a.count * a.n_det;
   const int n_items = n_series * NP;
   int n_mine = 0;  // items of this CTA: blockIdx.x + k gridDim.x
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) ++n_mine;
@@ -240,12 +241,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a) {
       tc_fence_after();
       const int item = blockIdx.x + k * gridDim.x;
       const int s = n_series - 1 - item / NP;
-      auto se = ep.series(s);
-      {
-        const float sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + s / a.n_det]));
-        se.ratio /= sc;  // exact: sc is a power of two
-        se.thr *= sc * sc;
+      RawEpi::Ser se;
+      float sc;
+      if constexpr (MP) {
+        const FilterPart& p = ps.p[part_of(ps, s, 1)];
+        const RawEpi pe{p.sel,         p.inv_sigma, p.thr_raw, nullptr,       p.pos0,  p.n_det,    a.window,
+                        p.valid_begin, p.valid_end, a.n_win,   p.n_sel_total, p.slots, p.row_valid};
+        se = pe.series(s - p.series0);
+        sc = series_scale16(__ldg(p.inv_sigma + p.sel[p.pos0 + (s - p.series0) / p.n_det]));
+      } else {
+        se = ep.series(s);
+        sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + s / a.n_det]));
       }
+      se.ratio /= sc;  // exact: sc is a power of two
+      se.thr *= sc * sc;
       const int64_t j1 = (int64_t)(item % NP) * kTcRows + r;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -301,23 +310,30 @@ int sm_count_tc() {
   return n;
 }
 
-}  // namespace
-
-cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st) {
-  if (a.n != (int64_t(1) << 20) || a.n1 != 1024 || a.n2 != 1024 || a.q_type != kBankF32 || !a.inter_f16)
-    return cudaErrorInvalidValue;
-  auto k = k_rows_tc<1024>;
+template <bool MP>
+cudaError_t run_rows_tc(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
+  auto k = k_rows_tc<1024, MP>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int items = a.count * a.n_det * (1024 / kTcRows);
+  const int items = (MP ? ps.n_series : a.count * a.n_det) * (1024 / kTcRows);
   const int g = sm_count_tc();  // one CTA (all 512 TMEM columns) per SM
-  cudaError_t e = launch_pdl_tc(k, items < g ? items : g, kTcThreads, kSMEM, st, a);
+  cudaError_t e = launch_pdl_tc(k, items < g ? items : g, kTcThreads, kSMEM, st, a, ps);
   add_launches(1);
   return e;
+}
+
+}  // namespace
+
+cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st, const FilterParts* parts) {
+  if (a.n != (int64_t(1) << 20) || a.n1 != 1024 || a.n2 != 1024 || a.q_type != kBankF32 || !a.inter_f16)
+    return cudaErrorInvalidValue;
+  if (parts) return run_rows_tc<true>(a, *parts, st);
+  const FilterParts one{};
+  return run_rows_tc<false>(a, one, st);
 }
 
 }  // namespace mf

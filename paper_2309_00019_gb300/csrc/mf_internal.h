@@ -68,6 +68,42 @@ struct FilterArgs {
 // rows per panel of the FP16 intermediate: a panel is one tensor-core row-pass item
 constexpr int kPanel16 = 8;
 
+// One plan's share of a fused launch (the length-class runner's work queue):
+// `count` templates from selection position pos0 against its n_det data rows,
+// the series [series0, series0 + count n_det) of the launch's scratch, in the
+// plan's (template, row) order.  Every part of a launch shares N, the storage
+// types (FP32 weighted data), the window, n_win, the intermediate and the
+// twiddle tables of the FilterArgs it is launched with.
+struct FilterPart {
+  const void* bank;
+  int64_t ld_bank;
+  const float2* q;
+  int64_t ld_q;
+  const int32_t* sel;
+  const float* inv_sigma;   // ratio per template id (as FilterArgs::inv_sigma)
+  const float* thr_raw;
+  int64_t pos0;
+  int count, n_det;
+  int64_t valid_begin, valid_end;
+  int64_t n_sel_total;
+  unsigned long long* slots;
+  const int2* row_valid;
+  int series0;
+};
+constexpr int kMaxParts = 8;
+struct FilterParts {
+  int n;         // parts of this launch, 1..kMaxParts (0: one plan, all of FilterArgs)
+  int n_series;  // series of all parts
+  FilterPart p[kMaxParts];
+};
+
+// part holding unit u of a launch whose parts own `per` consecutive units per series (uniform across a warp)
+__host__ __device__ inline int part_of(const FilterParts& ps, int64_t u, int per) {
+  int i = 0;
+  while (i + 1 < ps.n && u >= (int64_t)ps.p[i + 1].series0 * per) ++i;
+  return i;
+}
+
 // Quantise the FP32 weighted data q [n_det][ld_q] (nb bins per detector) to
 // 16-bit (q_type) q_lp with a per-detector power-of-two scale c_d chosen so that
 // max |c_d q| is in [2^14, 2^15); writes dscale[d] = c_d.  dmax: n_det words of
@@ -86,13 +122,29 @@ cudaError_t launch_quant_bank(const float2* src, int64_t ld_src, int64_t n_rows,
 int64_t plan_templates(const ::mf_plan_s* p);
 uint64_t plan_fingerprint(const ::mf_plan_s* p);
 bool plan_capturable(const ::mf_plan_s* p);
+// templates per launch pair of a plan's own filter (mf_set_batch)
+int plan_batch(const ::mf_plan_s* p);
+// Fused filter of several plans (the length-class runner's work queue): each plan filters its whole
+// bank against its own spectra dtilde[i] (rows ld[i] apart) exactly as mf_filter would, but the
+// two passes take the series of all plans in (plan, template, row) order, one launch pair per
+// scratch_series series across plan boundaries.  The plans share N, the window and the
+// intermediate, with an FP32 bank and FP32 data; `scratch` holds scratch_series series of the
+// intermediate (N x 8 bytes each; scratch_map encoded for it) and every step runs on st.  A wait
+// that times out is reported by plans[0].  On failure *err holds the message.
+int filter_fused(::mf_plan_s* const* plans, const void* const* dtilde, const int64_t* ld, int n_plans, void* scratch,
+                 int64_t scratch_series, const CUtensorMap& scratch_map, cudaStream_t st, std::string* err);
 // The TMA-staged filter passes (mf_filter.cu).  The bank rows and the
 // weighted data are in column layout: element k = k1 N2 + k2 of the non-zero
 // half (k1 < N1/2) at k2 N1/2 + k1 (see launch_to_cols).
 cudaError_t launch_filter2_pass1(const FilterArgs& a, cudaStream_t st);
 cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& scratch_map, cudaStream_t st);
 // the tensor-core row pass over the FP16 intermediate (mf_filter_tc.cu), N = 2^20
-cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st);
+cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st, const FilterParts* parts = nullptr);
+// Both passes over the series of several plans' parts in one launch each (ps.n >= 1): the
+// per-part fields come from ps, the rest (geometry, types, window, scratch, tables, status)
+// from a; the scratch holds ps.n_series series (scratch_map encoded for at least as many).
+cudaError_t launch_filter2_fused(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& scratch_map,
+                                 cudaStream_t st);
 // Tensor map of the pass-1 -> pass-2 scratch (`series` series of length n)
 // through which pass 2 reads its items; all zero where pass 2 needs none.
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m);

@@ -61,7 +61,7 @@ class mf_batch_trigger(C.Structure):
                 ("sample", C.c_int64), ("snr", C.c_float), ("phase", C.c_float)]
 
 
-MF_RUN_SERIAL, MF_RUN_STREAMS, MF_RUN_GRAPH = 0, 1, 2
+MF_RUN_SERIAL, MF_RUN_STREAMS, MF_RUN_GRAPH, MF_RUN_FUSED, MF_RUN_FUSED_GRAPH = 0, 1, 2, 3, 4
 BATCH_TRIGGER_NP = np.dtype([("det", np.int32), ("cls", np.int32), ("tmpl", np.int32), ("reserved", np.int32),
                              ("sample", np.int64), ("snr", np.float32), ("phase", np.float32)])
 
@@ -101,6 +101,7 @@ SIGNATURES = {
     "mf_batch_set_psd": (C.c_int, [_P, _P, _I64]),
     "mf_batch_set_segment": (C.c_int, [_P, C.c_int32, _I64, C.c_int32]),
     "mf_batch_autotune": (C.c_int, [_P, _P]),
+    "mf_batch_autotune_fused": (C.c_int, [_P, _P]),
     "mf_batch_segment": (C.c_int, [_P, C.c_int32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64),
                                    C.POINTER(_I64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mf_batch_plan": (C.c_int, [_P, C.c_int32, C.POINTER(_P)]),
@@ -481,9 +482,11 @@ class Batch:
     def set_segment(self, cls, n, per_launch=0):
         _bcheck(self.h, self.lib.mf_batch_set_segment(self.h, cls, n, per_launch))
 
-    def autotune(self, n_tmpl):
+    def autotune(self, n_tmpl, fused=False):
+        """Segment length and launch batch per class (fused: one segment length for all, for MF_RUN_FUSED)."""
         a = np.ascontiguousarray(n_tmpl, dtype=np.int64)
-        _bcheck(self.h, self.lib.mf_batch_autotune(self.h, a.ctypes.data))
+        fn = self.lib.mf_batch_autotune_fused if fused else self.lib.mf_batch_autotune
+        _bcheck(self.h, fn(self.h, a.ctypes.data))
 
     def segment(self, cls):
         v = [_I64() for _ in range(4)]
@@ -503,8 +506,13 @@ class Batch:
                          cuda_stream=None)
         return Plan.borrowed(h, d)
 
-    def run(self, strain, ld=None, mode=MF_RUN_GRAPH):
+    def run(self, strain, ld=None, mode=None):
+        """mf_batch_run; mode None: the fused work queue under a captured graph (MF_RUN_FUSED_GRAPH) when every
+        class with a plan has the same segment length, else the classes one after another (MF_RUN_SERIAL)."""
         ld = strain.shape[-1] if ld is None else ld
+        if mode is None:
+            ns = {self.segment(ci)["n"] for ci in range(self.n_class)} - {0}
+            mode = MF_RUN_FUSED_GRAPH if len(ns) == 1 else MF_RUN_SERIAL
         _bcheck(self.h, self.lib.mf_batch_run(self.h, _ptr(strain), ld, mode))
 
     def triggers(self):
