@@ -135,7 +135,12 @@ mf_status mf_gate_apply(const float* strain, int64_t ld, int32_t n_det, int64_t 
  * h~_t[k], row t at htilde + t*ld elements, k = 0..N/2 (ld >= N/2+1).  dtype
  * MF_F32 (scales must be NULL) or MF_F16 / MF_BF16 with host float32
  * scales[n_tmpl] (h~ = scale_t * stored value).  on_device != 0: htilde is a
- * device pointer, else host.  Copied into plan-owned device memory.  If the
+ * device pointer, else host.  Device rows are read on the plan's stream after
+ * the work already submitted to the legacy default stream (so rows written
+ * there, or on a blocking stream, are complete); rows written on another
+ * non-blocking stream must be complete before the call (the plans of an
+ * mf_batch_t run on the batch's own streams).  Copied into plan-owned device
+ * memory.  If the
  * PSD is set, sigma_t^2 = sum_k w[k] |h~_t[k]|^2 is computed in float64 on the
  * device (Eq. 2).  Errors: MF_EINVAL, MF_ENOMEM. */
 mf_status mf_load_bank(mf_plan_t plan, const void* htilde, mf_dtype dtype, int64_t n_tmpl, int64_t ld,

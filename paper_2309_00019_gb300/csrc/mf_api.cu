@@ -173,6 +173,18 @@ void dfree(T*& ptr) {
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// Device rows handed to a bank call are read on the plan's stream.  Order it after the work already
+// submitted to the legacy default stream, which every blocking stream's earlier work precedes: rows written
+// there (or on a blocking stream) before the call are complete when the plan reads them.
+cudaError_t after_default_stream(mf_plan_t p) {
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, cudaStreamLegacy);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  return e;
+}
+
 size_t elem_bytes(mf_dtype t) { return t == MF_F32 ? 8 : 4; }
 
 int bank_type(mf_dtype t) { return t == MF_F32 ? mf::kBankF32 : (t == MF_F16 ? mf::kBankF16 : mf::kBankBF16); }
@@ -399,7 +411,7 @@ mf_status mf_bank_set_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const void
   char* dst = (char*)p->bank + (size_t)row0 * p->ld_bank * eb;
   const void* src = htilde;
   void* tmp = nullptr;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = on_device ? after_default_stream(p) : cudaSuccess;
   if (!on_device) {  // stage host rows through a temporary device buffer
     mf_status s = dalloc(p, &tmp, (size_t)n_rows * ld * eb, "bank staging");
     if (s != MF_OK) return s;
@@ -430,7 +442,7 @@ mf_status mf_bank_quantize_rows(mf_plan_t p, int64_t row0, int64_t n_rows, const
   if (n_rows == 0) return MF_OK;
   const float2* src = (const float2*)htilde;
   float2* tmp = nullptr;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = on_device ? after_default_stream(p) : cudaSuccess;
   if (!on_device) {  // stage host rows through a temporary device buffer
     mf_status s = dalloc(p, &tmp, (size_t)n_rows * ld * sizeof(float2), "quantisation staging");
     if (s != MF_OK) return s;

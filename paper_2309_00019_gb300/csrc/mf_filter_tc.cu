@@ -214,31 +214,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
     for (int k = g; k < n_mine; k += kGroups) {
       const int slot = k % kSlots;
       unsigned char* sl = sm + slot * kItemBytes;
-      // twiddle w1024^{q u}, round to FP16, stage-2 operand row (u, r), K = (q, c), over the slot
-      // (warp-uniform outcome: the tensor-memory loads below are warp-collective)
-      if (!__all_sync(0xffffffffu, mbar_wait_at(d1 + g, par(k / kGroups), a.status, 14, k))) break;
-      tc_fence_after();
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int q = qg + 16 * h;
-        const float2* twq = tw + q * kTwStride;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {  // u = 16 c .. 16 c + 15
-          float y[32];
-          tmem_ld32(tbuf + 64 * h + 32 * c, y);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int u = 16 * c + i;
-            const float2 z = cmul(make_float2(y[2 * i], y[2 * i + 1]), twq[u]);
-            *reinterpret_cast<uint32_t*>(sl + cm_offset(u * 8 + r, 2 * q, kLbo, kSbo)) = pack_half2(z.x, z.y);
-          }
-        }
-      }
-      fence_proxy_async();  // our operand writes before the MMAs that read them
-      mbar_arrive(a2full + slot);
-      // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r
-      if (!__all_sync(0xffffffffu, mbar_wait_at(d2 + g, par(k / kGroups), a.status, 15, k))) break;
-      tc_fence_after();
+      // the item's series state first: its dependent global loads overlap the waits below
       const int item = blockIdx.x + k * gridDim.x;
       const int s = n_series - 1 - item / NP;
       RawEpi::Ser se;
@@ -256,22 +232,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
       se.ratio /= sc;  // exact: sc is a power of two
       se.thr *= sc * sc;
       const int64_t j1 = (int64_t)(item % NP) * kTcRows + r;
+      // twiddle w1024^{q u}, round to FP16, stage-2 operand row (u, r), K = (q, c), over the slot
+      // (warp-uniform outcome: the tensor-memory loads below are warp-collective)
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d1 + g, par(k / kGroups), a.status, 14, k))) break;
+      tc_fence_after();
+      // eight chunks of 16 columns (tile h = t / 4, u = 8 (t % 4) .. + 7); chunk t + 1 loads while t is used
+      float ya[16], yb[16];
+      tmem_ld16_issue(tbuf, ya);
+      tmem_wait(ya);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = qg + 16 * h;
+      for (int t = 0; t < 8; ++t) {
+        float(&cur)[16] = (t & 1) ? yb : ya;
+        float(&nxt)[16] = (t & 1) ? ya : yb;
+        if (t + 1 < 8) tmem_ld16_issue(tbuf + 64 * ((t + 1) >> 2) + 16 * ((t + 1) & 3), nxt);
+        const int q = qg + 16 * (t >> 2);
+        const float2* twq = tw + q * kTwStride;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {  // v = 16 c .. 16 c + 15
-          float z[32];
-          tmem_ld32(tbuf + 64 * h + 32 * c, z);
-          float mx = 0.f;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaf(z[2 * i], z[2 * i], z[2 * i + 1] * z[2 * i + 1]));
-          if (mx >= se.thr) {  // rare: some sample of this row is over the threshold
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              ep(se, j1 + (int64_t)N1 * (u + 32 * (16 * c + i)), make_float2(z[2 * i], z[2 * i + 1]));
-          }
+        for (int i = 0; i < 8; ++i) {
+          const int u = 8 * (t & 3) + i;
+          const float2 z = cmul(make_float2(cur[2 * i], cur[2 * i + 1]), twq[u]);
+          *reinterpret_cast<uint32_t*>(sl + cm_offset(u * 8 + r, 2 * q, kLbo, kSbo)) = pack_half2(z.x, z.y);
         }
+        if (t + 1 < 8) tmem_wait(nxt);
+      }
+      fence_proxy_async();  // our operand writes before the MMAs that read them
+      mbar_arrive(a2full + slot);
+      // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d2 + g, par(k / kGroups), a.status, 15, k))) break;
+      tc_fence_after();
+      float za[16], zb[16];
+      tmem_ld16_issue(tbuf, za);
+      tmem_wait(za);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {  // tile h = t / 4, v = 8 (t % 4) .. + 7
+        float(&cur)[16] = (t & 1) ? zb : za;
+        float(&nxt)[16] = (t & 1) ? za : zb;
+        if (t + 1 < 8) tmem_ld16_issue(tbuf + 64 * ((t + 1) >> 2) + 16 * ((t + 1) & 3), nxt);
+        const int u = qg + 16 * (t >> 2);
+        float mx = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fmaf(cur[2 * i], cur[2 * i], cur[2 * i + 1] * cur[2 * i + 1]));
+        if (mx >= se.thr) {  // rare: some sample of this row is over the threshold
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            ep(se, j1 + (int64_t)N1 * (u + 32 * (8 * (t & 3) + i)), make_float2(cur[2 * i], cur[2 * i + 1]));
+        }
+        if (t + 1 < 8) tmem_wait(nxt);
       }
       tc_fence_before();  // our tensor-memory reads before the MMAs that reuse the buffer
       mbar_arrive(tfree + g);

@@ -271,6 +271,9 @@ def test_fused_fp16_intermediate_matches_per_class(mf):
         b.set_segment(ci, 1 << 20, per)
     _load_banks(b, c)
     assert all(b.segment(ci)["n_seg"] == 2 for ci in range(3))
+    # rows written by torch just before the upload are complete when the class plan reads them
+    for ci in range(3):
+        assert np.all(b.plan(ci).sigmasq(len(c.class_ids(ci))) > 0), ci
     b.run(x, mode=mf.MF_RUN_FUSED)
     ref32 = b.triggers()[0]
     assert len(ref32) > 20 and len(np.unique(ref32["cls"])) >= 2
