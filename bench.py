@@ -41,7 +41,8 @@ WORKLOAD = ("two-stage hierarchical search: 2 det x 512 s @ 2048 Hz, coarse 2000
             "fine 20000 @ 2048 Hz (N=2^20) on the union of exact-match (>= 0.9) neighbourhoods")
 FP32_LANES_PER_SM = 128
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
-KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols_h16", "k_rows_tc")}  # k_cols_h16: k_cols with FP16 output
+# k_cols_h16 / k_cols_h16x2: k_cols with FP16 / FP16-pair output; k_rows_tc2: the split-product row pass
+KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols_h16", "k_rows_tc"), 4: ("k_cols_h16x2", "k_rows_tc2")}
 
 
 def measured_traffic(kernel, series_per_launch):
@@ -80,10 +81,10 @@ def parse():
                     help="instead of the benchmark, run two mf_filter calls on a 2-detector plan with N = 2^LOG2N "
                          "(a small, fixed case for profiler captures) and exit")
     ap.add_argument("--kernel-templates", type=int, default=16)
-    ap.add_argument("--intermediate", choices=["f32", "f16"], default="f16",
+    ap.add_argument("--intermediate", choices=["f32", "f16", "f16x2"], default="f16",
                     help="pass-1 -> pass-2 intermediate of the N = 2^20 (stage-2) filter: f16 (default; tensor-core "
-                         "row pass, SNR within 1e-3 of the FP64 oracle, the metric's bar) or f32 (ALU row pass, "
-                         "SNR within 1e-5)")
+                         "row pass, SNR within 1e-3 of the FP64 oracle, the metric's bar), f16x2 (FP16 pairs and "
+                         "split tensor-core products, FP32-level SNR) or f32 (ALU row pass, SNR within 1e-5)")
     return ap.parse_args()
 
 
@@ -108,8 +109,8 @@ def kernel_case(lg, n_tmpl, inter="f16"):
     p = mf.Plan(fs, n, 2, 30.0, fs / 2, 4.0, int(fs))
     p.set_psd(synth.psd_bins(n, fs))
     p.load_bank(bank)
-    if inter == "f16" and lg == 20:
-        p.set_intermediate(mf.MF_F16)
+    if inter != "f32" and lg == 20:
+        p.set_intermediate(mf.MF_F16 if inter == "f16" else mf.MF_F16X2)
     d = torch.from_numpy(fd).to(dev)
     p.filter(d)
     torch.cuda.synchronize()
@@ -374,8 +375,8 @@ def main():
         nb_ptr, nb_idx, _ = exact_nbhd_of_config(cfg.coarse_m1, cfg.coarse_m2, cfg.fine_m1, cfg.fine_m2, cfg.f_low,
                                                  cfg.fs2, device=dev)
     h = Hierarchy(hp, cfg.psd1, cfg.psd2, len(cfg.coarse_m1), len(cfg.fine_m1), nb_ptr, nb_idx, device=dev)
-    if args.intermediate == "f16":
-        h.p2.set_intermediate(mf.MF_F16)
+    if args.intermediate != "f32":
+        h.p2.set_intermediate(mf.MF_F16 if args.intermediate == "f16" else mf.MF_F16X2)
     for r0, rows in synth.taylorf2_chunks_torch(cfg.n1, cfg.fs1, cfg.coarse_m1, cfg.coarse_m2, cfg.f_low, dev,
                                                 chunk=256, ld=h.ld1):
         h.set_bank_rows(1, r0, rows)
@@ -531,7 +532,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.intermediate == "f32" else "f32 + f16 (f16 intermediate and tensor-core operands)",
+            "dtype": {"f32": "f32", "f16": "f32 + f16 (f16 intermediate and tensor-core operands)",
+                      "f16x2": "f32 + f16 pairs (hi + lo intermediate and tensor-core operands)"}[args.intermediate],
             "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.small else "scaled-down 32 s hierarchy (check run)",
                        "stage2_intermediate": args.intermediate,

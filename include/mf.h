@@ -39,7 +39,7 @@ typedef enum {
   MF_ETIMEOUT = 6      /* a bounded device wait gave up (reported, never trapped) */
 } mf_status;
 
-typedef enum { MF_F32 = 0, MF_F16 = 1, MF_BF16 = 2 } mf_dtype;
+typedef enum { MF_F32 = 0, MF_F16 = 1, MF_BF16 = 2, MF_F16X2 = 3 } mf_dtype;  /* MF_F16X2: intermediates only */
 
 /* Plan description.  The matched filter of Eq. (1)-(2) (Sec. II) on segments
  * of N samples: the analysis band is f_low <= f_k < f_high, 0 < k < N/2, and
@@ -217,9 +217,15 @@ mf_status mf_set_row_valid(mf_plan_t plan, const int64_t* range);
  * accumulation in tensor memory).  This halves the intermediate's HBM round
  * trip and moves the row transforms off the ALUs; SNR then agrees with the
  * FP64 filter to a few 1e-4 relative (within 1e-3) instead of 1e-6, so the
- * threshold and window peaks can differ at near-ties of that size.  Needs
- * FP32 weighted data (MF_F32 data dtype).  Synchronises.  Errors: MF_EINVAL
- * (dtype, or MF_F16 with N != 2^20). */
+ * threshold and window peaks can differ at near-ties of that size.  MF_F16X2
+ * (N = 2^20 only): each value as an FP16 pair hi + lo (hi = the value rounded
+ * to FP16, lo = the remainder rounded to FP16), 8 bytes per point like
+ * complex64, and the same tensor-core row pass with the stage operands and the
+ * DFT matrices split the same way: three products per step (hi hi, lo hi,
+ * hi lo), so each stage keeps about 22 significant bits and SNR stays at the
+ * FP32 path's level (1e-4 and better).  Needs FP32 weighted data (MF_F32 data
+ * dtype).  Synchronises.  Errors: MF_EINVAL (dtype, or MF_F16 / MF_F16X2 with
+ * N != 2^20). */
 mf_status mf_set_intermediate(mf_plan_t plan, mf_dtype dtype);
 
 /* Templates per pass-1/pass-2 launch pair (the batch; default: as many as
@@ -280,7 +286,8 @@ typedef struct {
   int64_t pass2_launches, pass2_series;
   double pass2_ms;
   int32_t impl;       /* filter kernels in use: 2 = k_cols / k_rows (FP32 intermediate), 3 = k_cols /
-                         k_rows_tc (FP16 intermediate, tensor-core row pass) */
+                         k_rows_tc (FP16 intermediate, tensor-core row pass), 4 = k_cols / k_rows_tc
+                         with FP16 pairs (MF_F16X2) */
   int32_t batch;      /* templates per pass-1 / pass-2 launch pair */
 } mf_plan_stats;
 

@@ -42,7 +42,7 @@ struct mf_plan_s {
   float2* q = nullptr;
   int64_t ld_q = 0;
   mf_dtype data_dtype = MF_F32;   // storage of the weighted data the filter reads
-  bool inter_f16 = false;         // FP16 pass-1 -> pass-2 intermediate and the tensor-core row pass
+  int inter = 0;                  // pass-1 -> pass-2 intermediate: 0 complex64, 1 FP16, 2 FP16 pairs (FilterArgs)
   void* q_lp = nullptr;           // 16-bit weighted data [n_det][ld_q]
   unsigned* dmax = nullptr;       // per-detector max |q| (float bits)
   float* dscale = nullptr;        // per-detector power-of-two data scale
@@ -109,7 +109,7 @@ uint64_t plan_fingerprint(const mf_plan_s* p) {
   mix((uint64_t)p->n_tmpl);
   mix((uint64_t)p->batch);
   mix((uint64_t)p->data_dtype);
-  mix((uint64_t)p->inter_f16);
+  mix((uint64_t)p->inter);
   mix((uint64_t)(uintptr_t)p->row_valid);
   mix((uint64_t)(uintptr_t)p->scratch);
   mix((uint64_t)(uintptr_t)p->slots);
@@ -522,11 +522,12 @@ mf_status mf_bank_generate_taylorf2(mf_plan_t p, int64_t row0, int64_t n_rows, c
 
 mf_status mf_set_intermediate(mf_plan_t p, mf_dtype dtype) {
   if (!p) return fail(p, MF_EINVAL, "mf_set_intermediate: null plan");
-  if (dtype != MF_F32 && dtype != MF_F16) return fail(p, MF_EINVAL, "mf_set_intermediate: dtype must be F32 or F16");
-  if (dtype == MF_F16 && p->d.n != (int64_t(1) << 20))
-    return fail(p, MF_EINVAL, "mf_set_intermediate: the FP16 intermediate needs N = 2^20");
+  if (dtype != MF_F32 && dtype != MF_F16 && dtype != MF_F16X2)
+    return fail(p, MF_EINVAL, "mf_set_intermediate: dtype must be F32, F16 or F16X2");
+  if (dtype != MF_F32 && p->d.n != (int64_t(1) << 20))
+    return fail(p, MF_EINVAL, "mf_set_intermediate: the FP16 intermediates need N = 2^20");
   cudaStreamSynchronize(p->st);
-  p->inter_f16 = dtype == MF_F16;
+  p->inter = dtype == MF_F32 ? 0 : (dtype == MF_F16 ? 1 : 2);
   return MF_OK;
 }
 
@@ -629,7 +630,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   if (n_subset > 0 && !subset) return fail(p, MF_EINVAL, "mf_filter: subset is NULL");
   if (p->data_dtype != MF_F32 && p->data_dtype != p->bank_dtype)
     return fail(p, MF_EINVAL, "mf_filter: 16-bit data need a bank of the same 16-bit type");
-  if (p->inter_f16 && p->data_dtype != MF_F32)
+  if (p->inter && p->data_dtype != MF_F32)
     return fail(p, MF_EINVAL, "mf_filter: the FP16 intermediate needs FP32 weighted data");
   const int64_t n_sel = n_subset < 0 ? p->n_tmpl : n_subset;
   mf_status s = ensure_slots(p, std::max<int64_t>(n_sel, 1));
@@ -682,7 +683,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
   a.q_type = bank_type(p->data_dtype);
   a.q_lp = p->q_lp;
   a.dscale = p->dscale;
-  a.inter_f16 = p->inter_f16 ? 1 : 0;
+  a.inter = p->inter;
   LaunchScope ls(p);
   ls.before = launches_before;
   for (int64_t pos0 = 0; pos0 < n_sel; pos0 += p->batch) {
@@ -741,7 +742,7 @@ mf_status mf_get_stats(mf_plan_t p, mf_plan_stats* out, int reset) {
     p->stats.pass2_ms += t2;
   }
   p->samples.clear();
-  p->stats.impl = p->inter_f16 ? 3 : 2;
+  p->stats.impl = 2 + p->inter;
   p->stats.batch = p->batch;
   *out = p->stats;
   if (reset) p->stats = mf_plan_stats{};
@@ -1064,7 +1065,7 @@ int filter_fused(mf_plan_s* const* plans, const void* const* dtilde, const int64
     if (!p || !dtilde[i]) return bad(MF_EINVAL, "fused filter: null plan or data");
     if (!p->psd_set || !p->bank || p->n_tmpl == 0) return bad(MF_ESTATE, "fused filter: a plan has no PSD or bank");
     if (ld[i] < p->nb) return bad(MF_EINVAL, "fused filter: ld_dtilde < N/2+1");
-    if (p->d.n != p0->d.n || p->bank_dtype != MF_F32 || p->data_dtype != MF_F32 || p->inter_f16 != p0->inter_f16 ||
+    if (p->d.n != p0->d.n || p->bank_dtype != MF_F32 || p->data_dtype != MF_F32 || p->inter != p0->inter ||
         p->d.window != p0->d.window || p->n_win != p0->n_win)
       return bad(MF_EINVAL, "fused filter: the plans differ in N, window or intermediate, or store 16-bit data");
     if (p->d.n_det > scratch_series) return bad(MF_EINVAL, "fused filter: scratch smaller than a plan's rows");
@@ -1100,7 +1101,7 @@ int filter_fused(mf_plan_s* const* plans, const void* const* dtilde, const int64
   a.tw2 = p0->tw + 1024;
   a.tw4 = p0->tw4;
   a.q_type = kBankF32;
-  a.inter_f16 = p0->inter_f16 ? 1 : 0;
+  a.inter = p0->inter;
   // the work queue: (plan, template, row) series in order, cut into launches of at most scratch_series
   int i = 0;
   int64_t t = 0;

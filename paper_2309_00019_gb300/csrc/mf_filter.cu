@@ -145,7 +145,6 @@ struct RowGeo {
 // P = RW.
 template <int N1, int N2>
 struct ScratchGeo {
-  static constexpr int RA = SubFft<N1>::RA;
   static constexpr int RW = RowGeo<N2>::RW;
   static constexpr int HT = SubFft<N1>::T / 2;
   static constexpr int P = HT > RW ? HT : RW;
@@ -178,14 +177,18 @@ __global__ void k_fill_twiddles(float2* tw) {
 // pass 1
 // ---------------------------------------------------------------------------
 
-// H16: FP16 intermediate, each series scaled by series_scale16 of its template, in panels of kPanel16
-// rows that are the tensor-core row pass's stage-1 operand image: with k2 = 32 p + q, part c (0 real,
-// 1 imaginary) of element (j1, k2) is the half at panel j1 / 8, ((q 32 + p) 2 + c) 8 + j1 % 8 (panels of
-// 2 N2 8 halves), i.e. the MN-major layout of rows m = 8 q + j1 % 8 and columns k = 2 p + c
+// IM: the intermediate (FilterArgs::inter).  IM >= 1: FP16, each series scaled by series_scale16 of its
+// template, in panels of kPanel16 rows that are the tensor-core row pass's stage-1 operand image: with
+// k2 = 32 p + q, part c (0 real, 1 imaginary) of element (j1, k2) is the half at panel j1 / 8,
+// ((q 32 + p) 2 + c) 8 + j1 % 8 (an image of 2 N2 8 halves), i.e. the MN-major layout of rows
+// m = 8 q + j1 % 8 and columns k = 2 p + c.  IM = 2: each panel holds the image of hi = the value rounded
+// to FP16, then the image of lo = the remainder rounded to FP16.
 // MP: the series of several plans' parts (FilterParts), each with its own bank, data rows and selection
-template <int N1, int N2, int BT, int QT, bool H16, bool MP>
+template <int N1, int N2, int BT, int QT, int IM, bool MP>
 __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a, const __grid_constant__ FilterParts ps) {
   static_assert(!MP || QT == kBankF32, "fused launches take FP32 weighted data");
+  constexpr bool H16 = IM >= 1;
+  constexpr int IMG = IM == 2 ? 2 : 1;  // FP16 images per panel
   using G = SubFft<N1>;
   using P = ColGeo<N1, BT, QT>;
   constexpr int RA = G::RA, RB = G::RB, T = G::T, NB = G::NB, C = P::C, R = P::R, S = P::S;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a, const __g
     for (int q = 0; q < RA; ++q) xb[ta * RA + q + ta] = v[q];
     __syncwarp();
     float2* out = a.scratch + (int64_t)s * N;
-    __half* out16 = reinterpret_cast<__half*>(a.scratch) + (int64_t)s * 2 * N;
+    __half* out16 = reinterpret_cast<__half*>(a.scratch) + (int64_t)s * 2 * IMG * N;
     const int k2 = ((li / nd) % NCB) * C + ca;
     float sc = 1.f;
     if constexpr (H16) sc = series_scale16(__ldg(isg + sel[pos0 + li / (nd * NCB)]));
@@ -337,15 +340,24 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols(FilterArgs a, const __g
         // of rows j, j + 1 and j + 1 their imaginary parts (one warp store: four whole 32-byte sectors)
         static_assert(T == 32, "lane pairs");
         const bool odd = (j & 1) != 0;
-        __half* ob = out16 + (int64_t)(j / PH) * (2 * N2 * PH) + (((k2 & 31) * 32 + (k2 >> 5)) * 2) * PH +
+        constexpr int64_t IMAGE = 2 * N2 * PH;  // halves of one FP16 image of a panel
+        __half* ob = out16 + (int64_t)(j / PH) * (IMG * IMAGE) + (((k2 & 31) * 32 + (k2 >> 5)) * 2) * PH +
                      (odd ? PH + (j % PH) - 1 : (j % PH));
-#pragma unroll
-        for (int q = 0; q < RB; ++q) {
-          const __half2 h = __float22half2_rn(cmul(u[q], w));
+        auto pair_store = [&](__half* dst, __half2 h) {
           const uint32_t mine = *reinterpret_cast<const uint32_t*>(&h);
           const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-          const uint32_t v = odd ? __byte_perm(other, mine, 0x7632) : __byte_perm(mine, other, 0x5410);
-          *reinterpret_cast<uint32_t*>(ob + (int64_t)q * (RA / PH) * (2 * N2 * PH)) = v;
+          *reinterpret_cast<uint32_t*>(dst) = odd ? __byte_perm(other, mine, 0x7632) : __byte_perm(mine, other, 0x5410);
+        };
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const float2 z = cmul(u[q], w);
+          const __half2 h = __float22half2_rn(z);
+          __half* dq = ob + (int64_t)q * (RA / PH) * (IMG * IMAGE);
+          pair_store(dq, h);
+          if constexpr (IM == 2) {  // the remainder: z - hi is exact in FP32
+            const float2 hf = __half22float2(h);
+            pair_store(dq + IMAGE, __float22half2_rn(make_float2(z.x - hf.x, z.y - hf.y)));
+          }
           if (q + 1 < RB) w = cmul(w, st);
         }
       } else if constexpr (RA % PH == 0) {  // j1 = j + q RA: q RA / PH whole panels past j's
@@ -521,11 +533,11 @@ int grid2(int items) {
   return items < g ? items : g;
 }
 
-template <int N1, int N2, int BT, int QT, bool H16 = false, bool MP = false>
+template <int N1, int N2, int BT, int QT, int IM = 0, bool MP = false>
 cudaError_t run_cols(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
   using P = ColGeo<N1, BT, QT>;
   static_assert(P::SMEM * 3 <= 230400, "k_cols: three CTAs per SM must fit in shared memory");
-  auto k = k_cols<N1, N2, BT, QT, H16, MP>;
+  auto k = k_cols<N1, N2, BT, QT, IM, MP>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem2(k, P::SMEM);
@@ -545,20 +557,31 @@ cudaError_t run_cols_bt(const FilterArgs& a, const FilterParts& ps, cudaStream_t
   const bool mp = ps.n > 0;
   if (mp && (a.q_type != kBankF32 || a.bank_type != kBankF32)) return cudaErrorInvalidValue;
   if constexpr (N1 == 1024 && N2 == 1024) {
-    if (a.inter_f16) {  // FP16 intermediate for the tensor-core row pass: FP32 data, any bank
-      if (a.q_type != kBankF32) return cudaErrorInvalidValue;
-      if (mp) return run_cols<N1, N2, kBankF32, kBankF32, true, true>(a, ps, st);
+    // FP16 intermediates for the tensor-core row pass: FP32 data, any bank
+    if (a.inter != 0 && a.q_type != kBankF32) return cudaErrorInvalidValue;
+    if (a.inter == 1) {
+      if (mp) return run_cols<N1, N2, kBankF32, kBankF32, 1, true>(a, ps, st);
       switch (a.bank_type) {
-        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, true>(a, ps, st);
-        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, true>(a, ps, st);
-        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, true>(a, ps, st);
+        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, 1>(a, ps, st);
+        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, 1>(a, ps, st);
+        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, 1>(a, ps, st);
       }
       return cudaErrorInvalidValue;
     }
+    if (a.inter == 2) {
+      if (mp) return run_cols<N1, N2, kBankF32, kBankF32, 2, true>(a, ps, st);
+      switch (a.bank_type) {
+        case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32, 2>(a, ps, st);
+        case kBankF16: return run_cols<N1, N2, kBankF16, kBankF32, 2>(a, ps, st);
+        case kBankBF16: return run_cols<N1, N2, kBankBF16, kBankF32, 2>(a, ps, st);
+      }
+      return cudaErrorInvalidValue;
+    }
+    if (a.inter != 0) return cudaErrorInvalidValue;
   } else {
-    if (a.inter_f16) return cudaErrorInvalidValue;
+    if (a.inter != 0) return cudaErrorInvalidValue;
   }
-  if (mp) return run_cols<N1, N2, kBankF32, kBankF32, false, true>(a, ps, st);
+  if (mp) return run_cols<N1, N2, kBankF32, kBankF32, 0, true>(a, ps, st);
   if (a.q_type == kBankF32) {
     switch (a.bank_type) {
       case kBankF32: return run_cols<N1, N2, kBankF32, kBankF32>(a, ps, st);
@@ -689,7 +712,7 @@ cudaError_t pass1_parts(const FilterArgs& a, const FilterParts& ps, cudaStream_t
 }
 
 cudaError_t pass2_parts(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
-  if (a.inter_f16) return launch_filter2_pass2_tc(a, st, ps.n > 0 ? &ps : nullptr);
+  if (a.inter != 0) return launch_filter2_pass2_tc(a, st, ps.n > 0 ? &ps : nullptr);
   MF_DISPATCH2(a.n, run_rows, (a, ps, tm, st))
 }
 

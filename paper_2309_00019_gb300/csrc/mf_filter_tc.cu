@@ -44,63 +44,76 @@ constexpr int kTcRows = kPanel16;                 // rows per item
 constexpr int kTcK = 64;                          // 32 complex values, real and imaginary interleaved
 constexpr int kLbo = 128, kSbo = 1024;            // unpadded core-matrix layouts
 constexpr int kTileBytes = 128 * kTcK * 2;        // one M = 128 operand tile, 16 KB
-constexpr int kItemBytes = 2 * kTileBytes;        // one item (256 rows), 32 KB
-constexpr int kSlots = 6;                         // operand slots
-constexpr int kB_OFF = kSlots * kItemBytes;       // B: 64 x 64, 8 KB
+constexpr int kBBytes = 64 * kTcK * 2;            // one image of the DFT matrix B (64 x 64), 8 KB
 constexpr int kTwStride = 33;                     // padded rows of the w1024^{q u} table (float2)
-constexpr int kTW_OFF = kB_OFF + 64 * kTcK * 2;
-constexpr int kBAR_OFF = kTW_OFF + 32 * kTwStride * 8;
-constexpr int kNBar = 3 * kSlots + 3 * kGroups + 1;
-constexpr int kSMEM = kBAR_OFF + kNBar * 8 + 16;
 constexpr uint32_t kBufCols = 128;                // 2 tiles x 64 FP32 columns
 constexpr uint32_t kTmemCols = kGroups * kBufCols;  // all 512
 constexpr uint32_t kIdesc2 = tc_idesc_f16(128, 64);          // A K-major (stage 2)
 constexpr uint32_t kIdesc1 = kIdesc2 | (1u << 15);           // A MN-major (stage 1)
 
-static_assert(cm_offset(255, 63, kLbo, kSbo) + 2 <= kItemBytes, "A2 layout");
-static_assert(kSMEM <= 232448, "k_rows_tc shared memory");
+static_assert(cm_offset(255, 63, kLbo, kSbo) + 2 <= 2 * kTileBytes, "A2 layout");
+
+// Shared memory: operand slots, B (hi, then lo when split), the twiddle table, the barriers.  SPLIT: every
+// operand and B is a pair of FP16 images (hi, then lo), so an item is 64 KB and three slots fit.
+template <bool SPLIT>
+struct TcGeo {
+  static constexpr int IMG = SPLIT ? 2 : 1;         // FP16 images per operand
+  static constexpr int ITEM = IMG * 2 * kTileBytes;  // one item: 256 rows of every image
+  static constexpr int SLOTS = SPLIT ? 3 : 6;
+  static constexpr int B_OFF = SLOTS * ITEM;
+  static constexpr int TW_OFF = B_OFF + IMG * kBBytes;
+  static constexpr int BAR_OFF = TW_OFF + 32 * kTwStride * 8;
+  static constexpr int NBAR = 3 * SLOTS + 3 * kGroups + 1;
+  static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
+  static_assert(SMEM <= 232448, "k_rows_tc shared memory");
+};
 
 // generic-proxy writes of another grid -> async-proxy (bulk copy) reads of this one
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pack_half2(float re, float im) {
-  __half2 h = __floats2half2_rn(re, im);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// 8 MMAs of one stage: two M = 128 tiles x four K = 16 steps into buffer columns [d, d + 128)
+// One stage: two M = 128 tiles x four K = 16 steps into buffer columns [d, d + 128), 8 MMAs.  SPLIT: per
+// step also A lo x B hi and A hi x B lo (the A lo image two tiles on, B lo one B image on), 24 MMAs.
+template <bool SPLIT>
 __device__ __forceinline__ void stage_mmas(uint32_t d, uint32_t a_addr, bool mn_major, uint32_t b_addr) {
+  const uint32_t idesc = mn_major ? kIdesc1 : kIdesc2;
 #pragma unroll
   for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int ks = 0; ks < kTcK / 16; ++ks) {
       // K steps: two core matrices along K, 128 B apart in both operand layouts
-      const uint64_t ad = tc_desc(a_addr + h * kTileBytes + ks * 2 * kLbo, kLbo, kSbo);
-      const uint64_t bd = tc_desc(b_addr + ks * 2 * kLbo, kLbo, kSbo);
-      tc_mma_f16(d + 64 * h, ad, bd, mn_major ? kIdesc1 : kIdesc2, ks > 0);
+      const uint32_t ao = h * kTileBytes + ks * 2 * kLbo, bo = ks * 2 * kLbo;
+      const uint64_t ad = tc_desc(a_addr + ao, kLbo, kSbo), bd = tc_desc(b_addr + bo, kLbo, kSbo);
+      tc_mma_f16(d + 64 * h, ad, bd, idesc, ks > 0);
+      if constexpr (SPLIT) {
+        tc_mma_f16(d + 64 * h, tc_desc(a_addr + 2 * kTileBytes + ao, kLbo, kSbo), bd, idesc, true);
+        tc_mma_f16(d + 64 * h, ad, tc_desc(b_addr + kBBytes + bo, kLbo, kSbo), idesc, true);
+      }
     }
 }
 
 // parity of the n-th completion (n = 0, 1, ...) of a barrier
 __device__ __forceinline__ uint32_t par(int n) { return (uint32_t)(n & 1); }
 
-// MP: the series of several plans' parts (FilterParts), each with its own epilogue state
-template <int N1, bool MP>
+// MP: the series of several plans' parts (FilterParts), each with its own epilogue state.  SPLIT: the FP16-pair
+// intermediate (FilterArgs::inter = 2) and split products.
+template <int N1, bool MP, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const __grid_constant__ FilterParts ps) {
+  using G = TcGeo<SPLIT>;
+  constexpr int kSlots = G::SLOTS, kItemBytes = G::ITEM;
   constexpr int N2 = 1024;
   constexpr int64_t N = (int64_t)N1 * N2;
   constexpr int NP = N1 / kTcRows;  // panels (items) per series
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sB = sm + kB_OFF;
-  float2* tw = reinterpret_cast<float2*>(sm + kTW_OFF);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kBAR_OFF);  // [kSlots]
+  unsigned char* sB = sm + G::B_OFF;
+  float2* tw = reinterpret_cast<float2*>(sm + G::TW_OFF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + G::BAR_OFF);  // [kSlots]
   uint64_t* a2full = full + kSlots;                              // [kSlots]
   uint64_t* empty = a2full + kSlots;                             // [kSlots]
   uint64_t* d1 = empty + kSlots;                                 // [kGroups]
   uint64_t* d2 = d1 + kGroups;
   uint64_t* tfree = d2 + kGroups;
   uint64_t* drain = tfree + kGroups;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBAR_OFF + kNBar * 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::BAR_OFF + G::NBAR * 8);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   const int n_series = MP ? ps.n_series : a.count * a.n_det;
   const int n_items = n_series * NP;
@@ -108,12 +121,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) ++n_mine;
 
   if (warp == kMmaWarp) tmem_alloc(tslot, kTmemCols);
-  // B: the embedded DFT matrix, B[(u, c)][(p, c')] = Re / Im parts of w32^{p u}
+  // B: the embedded DFT matrix, B[(u, c)][(p, c')] = Re / Im parts of w32^{p u} (SPLIT: hi, then lo)
   for (int i = tid; i < 64 * kTcK; i += kTcThreads) {
     const int n = i / kTcK, k = i % kTcK, u = n >> 1, c = n & 1, p = k >> 1, cp = k & 1;
     const float2 f = unit_root((uint32_t)((p * u) & 31), 32u);
     const float v = c == 0 ? (cp == 0 ? f.x : -f.y) : (cp == 0 ? f.y : f.x);
-    *reinterpret_cast<__half*>(sB + cm_offset(n, k, kLbo, kSbo)) = __float2half_rn(v);
+    const __half hi = __float2half_rn(v);
+    *reinterpret_cast<__half*>(sB + cm_offset(n, k, kLbo, kSbo)) = hi;
+    if constexpr (SPLIT)
+      *reinterpret_cast<__half*>(sB + kBBytes + cm_offset(n, k, kLbo, kSbo)) = __float2half_rn(v - __half2float(hi));
   }
   for (int i = tid; i < 32 * 32; i += kTcThreads) {
     const int q = i >> 5, u = i & 31;
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
   const __half* scratch = reinterpret_cast<const __half*>(a.scratch);
 
   if (warp == kProdWarp) {
-    // ---- producer: item k into slot k % 6 once stage 2 of item k - 6 has read that slot ----
+    // ---- producer: item k into slot k % kSlots once stage 2 of item k - kSlots has read that slot ----
     if (lane == 0) {
       pdl_wait();  // the intermediate is written by the kernel just before
       fence_proxy_async_global();
@@ -152,7 +168,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
         if (k >= kSlots && !(ok = mbar_wait_at(empty + slot, par(k / kSlots - 1), a.status, 11, k))) break;
         const int item = blockIdx.x + k * gridDim.x;
         const int s = n_series - 1 - item / NP;  // series in reverse: the last ones written are likeliest in L2
-        const __half* src = scratch + (int64_t)s * 2 * N + (int64_t)(item % NP) * (2 * N2 * kTcRows);
+        const __half* src =
+            scratch + (int64_t)s * 2 * G::IMG * N + (int64_t)(item % NP) * (2 * G::IMG * N2 * kTcRows);
         mbar_expect_tx(full + slot, (uint32_t)kItemBytes);
         bulk_g2s(sm + slot * kItemBytes, src, (uint32_t)kItemBytes, full + slot);
       }
@@ -174,7 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
           if (mbar_test_wait(full + slot, par(n1 / kSlots)) &&
               (n1 < kGroups || mbar_test_wait(tfree + g, par(n1 / kGroups - 1)))) {
             tc_fence_after();
-            stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
+            stage_mmas<SPLIT>(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
             tc_commit(d1 + g);
             ++n1;
             progress = true;
@@ -184,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
           const int slot = n2 % kSlots, g = n2 % kGroups;
           if (mbar_test_wait(a2full + slot, par(n2 / kSlots))) {
             tc_fence_after();
-            stage_mmas(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
+            stage_mmas<SPLIT>(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
             tc_commit(d2 + g);
             tc_commit(empty + slot);
             ++n2;
@@ -251,7 +268,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
         for (int i = 0; i < 8; ++i) {
           const int u = 8 * (t & 3) + i;
           const float2 z = cmul(make_float2(cur[2 * i], cur[2 * i + 1]), twq[u]);
-          *reinterpret_cast<uint32_t*>(sl + cm_offset(u * 8 + r, 2 * q, kLbo, kSbo)) = pack_half2(z.x, z.y);
+          const int off = cm_offset(u * 8 + r, 2 * q, kLbo, kSbo);
+          const __half2 hi = __floats2half2_rn(z.x, z.y);
+          *reinterpret_cast<__half2*>(sl + off) = hi;
+          if constexpr (SPLIT) {  // the remainder, exact in FP32, into the lo image two tiles on
+            const float2 hf = __half22float2(hi);
+            *reinterpret_cast<__half2*>(sl + 2 * kTileBytes + off) = __floats2half2_rn(z.x - hf.x, z.y - hf.y);
+          }
         }
         if (t + 1 < 8) tmem_wait(nxt);
       }
@@ -316,18 +339,19 @@ int sm_count_tc() {
   return n;
 }
 
-template <bool MP>
+template <bool MP, bool SPLIT>
 cudaError_t run_rows_tc(const FilterArgs& a, const FilterParts& ps, cudaStream_t st) {
-  auto k = k_rows_tc<1024, MP>;
+  using G = TcGeo<SPLIT>;
+  auto k = k_rows_tc<1024, MP, SPLIT>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSMEM);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int items = (MP ? ps.n_series : a.count * a.n_det) * (1024 / kTcRows);
   const int g = sm_count_tc();  // one CTA (all 512 TMEM columns) per SM
-  cudaError_t e = launch_pdl_tc(k, items < g ? items : g, kTcThreads, kSMEM, st, a, ps);
+  cudaError_t e = launch_pdl_tc(k, items < g ? items : g, kTcThreads, G::SMEM, st, a, ps);
   add_launches(1);
   return e;
 }
@@ -335,11 +359,12 @@ cudaError_t run_rows_tc(const FilterArgs& a, const FilterParts& ps, cudaStream_t
 }  // namespace
 
 cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st, const FilterParts* parts) {
-  if (a.n != (int64_t(1) << 20) || a.n1 != 1024 || a.n2 != 1024 || a.q_type != kBankF32 || !a.inter_f16)
+  if (a.n != (int64_t(1) << 20) || a.n1 != 1024 || a.n2 != 1024 || a.q_type != kBankF32 ||
+      (a.inter != 1 && a.inter != 2))
     return cudaErrorInvalidValue;
-  if (parts) return run_rows_tc<true>(a, *parts, st);
   const FilterParts one{};
-  return run_rows_tc<false>(a, one, st);
+  if (a.inter == 2) return parts ? run_rows_tc<true, true>(a, *parts, st) : run_rows_tc<false, true>(a, one, st);
+  return parts ? run_rows_tc<true, false>(a, *parts, st) : run_rows_tc<false, false>(a, one, st);
 }
 
 }  // namespace mf

@@ -60,9 +60,10 @@ struct FilterArgs {
   const float* dscale;
   // per data row analysed range [x, y) (TMA kernels), or null: [valid_begin, valid_end) for all rows
   const int2* row_valid;
-  // 1: FP16 pass-1 -> pass-2 intermediate in kPanel16-row panels, each series scaled by
-  // series_scale16(ratio[template]), and the tensor-core row pass (N = 2^20 only)
-  int inter_f16;
+  // pass-1 -> pass-2 intermediate (N = 2^20 only for 1 and 2): 0 complex64, ALU row pass; 1 FP16 in
+  // kPanel16-row panels, each series scaled by series_scale16(ratio[template]), tensor-core row pass;
+  // 2 the same with every value an FP16 pair (hi image, then lo image, per panel) and split products
+  int inter;
 };
 
 // rows per panel of the FP16 intermediate: a panel is one tensor-core row-pass item

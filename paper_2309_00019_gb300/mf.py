@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmf.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ESTATE, MF_EOVERFLOW, MF_ETIMEOUT = range(7)
-MF_F32, MF_F16, MF_BF16 = 0, 1, 2
+MF_F32, MF_F16, MF_BF16, MF_F16X2 = 0, 1, 2, 3  # MF_F16X2: intermediates only (FP16 pairs)
 STATUS_NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_ESTATE", 5: "MF_EOVERFLOW",
                 6: "MF_ETIMEOUT"}
 

@@ -286,6 +286,16 @@ def test_fused_fp16_intermediate_matches_per_class(mf):
         assert np.array_equal(b.triggers()[0], ref16), mode
     s = _compare_f16(ref16, ref32, c.thr, c.window)
     print(f"\nFP16 vs FP32 fused: {s}")
+    # FP16 pairs with split products: fused and per class bit for bit, at the FP32 bar against FP32
+    for ci in range(3):
+        b.plan(ci).set_intermediate(mf.MF_F16X2)
+    b.run(x, mode=mf.MF_RUN_STREAMS)
+    ref2 = b.triggers()[0]
+    for mode in (mf.MF_RUN_FUSED, mf.MF_RUN_FUSED_GRAPH):
+        b.run(x, mode=mode)
+        assert np.array_equal(b.triggers()[0], ref2), mode
+    s = _compare_f16(ref2, ref32, c.thr, c.window, rel_tie=2e-4, snr_rtol=1e-4)
+    print(f"FP16 pairs vs FP32 fused: {s}")
 
 
 def _compare_f16(t16, t32, thr, window, rel_tie=2e-3, snr_rtol=1e-3):

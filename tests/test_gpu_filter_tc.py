@@ -4,7 +4,9 @@ peak of every template in coloured noise with a loud glitch and a TaylorF2
 injection, SNR within 1e-3 relative (the workload's SNR-error bar) with the
 near-tie allowances scaled to that bar; the injected template's peak at its
 sample with rho = A sigma; several launches per call, subsets, one and two
-detectors; agreement with the FP32 path; and the argument checks."""
+detectors; agreement with the FP32 path; and the argument checks.  The same
+for the FP16-pair intermediate with split tensor-core products
+(mf_set_intermediate(MF_F16X2)) at the FP32 path's bar, 1e-4."""
 
 import math
 
@@ -21,6 +23,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 N, FS, F_LOW = 1 << 20, 2048.0, 30.0
 SNR_RTOL, REL_TIE = 1e-3, 2e-3  # rho to 1e-3, so rho^2 ties and threshold edges to 2e-3
+SPLIT_RTOL, SPLIT_TIE = 1e-4, 2e-4  # FP16 pairs: the FP32 bar
 
 
 @pytest.fixture(scope="module")
@@ -129,12 +132,63 @@ def test_tc_row_pass_agrees_with_the_fp32_path(case):
           f"max rel SNR diff {worst:.2e}")
 
 
+def test_split_row_pass_matches_the_oracle_at_the_fp32_bar(case):
+    from paper_2309_00019_gb300 import mf
+
+    trig, n, st = _filter(mf, case, inter=mf.MF_F16X2)
+    assert st["impl"] == 4 and n == len(trig) > 0
+    ids = list(range(len(case["bank_np"])))
+    res = compare_triggers(trig, case["rho2"], ids, 4.0, int(FS), rel_tie=SPLIT_TIE, snr_rtol=SPLIT_RTOL,
+                           phase_atol=0.01, z=case["z"])
+    assert res["exact"] > 0.99 * n
+    i = np.nonzero((trig["det"] == 1) & (trig["tmpl"] == case["inj"]) & (trig["sample"] == case["j0"]))[0]
+    assert len(i) == 1
+    assert trig["snr"][trig["det"] == 0].max() > 100
+    print(f"\nFP16-pair intermediate + split tensor-core products: {n} triggers, {res}")
+
+
+def test_split_row_pass_noiseless_injection_and_batches(case):
+    from paper_2309_00019_gb300 import mf
+
+    bank_np, inj, j0 = case["bank_np"], case["inj"], case["j0"]
+    w = O.weights(N, FS, F_LOW, FS / 2, case["psd"])
+    amp = case["snr_inj"] / math.sqrt(O.sigmasq(bank_np[inj].astype(np.complex128), w))
+    k = np.arange(N // 2 + 1)
+    d = (amp * bank_np[inj].astype(np.complex128) * np.exp(-2j * np.pi * k * j0 / N))[None].astype(np.complex64)
+    c = dict(case, fd=np.concatenate([d, d]))
+    trig, n, st = _filter(mf, c, n_det=1, inter=mf.MF_F16X2, subset=[inj], thr=6.0)
+    i = np.nonzero(trig["sample"] == j0)[0]
+    assert st["impl"] == 4 and len(i) == 1 and abs(trig["snr"][i[0]] / case["snr_inj"] - 1) < 1e-5, trig
+    sub = [11, 3, 7, 0, 5]
+    trig, n, st = _filter(mf, case, n_det=1, inter=mf.MF_F16X2, batch=2, subset=sub)
+    res = compare_triggers(trig, case["rho2"][1:, sub], sub, 4.0, int(FS), rel_tie=SPLIT_TIE, snr_rtol=SPLIT_RTOL)
+    assert n > 0 and res["exact"] > 0.99 * n
+
+
+def test_split_row_pass_agrees_with_the_fp32_path(case):
+    from paper_2309_00019_gb300 import mf
+
+    a, na, sa = _filter(mf, case, inter=mf.MF_F16X2)
+    b, nb, sb = _filter(mf, case)
+    assert sa["impl"] == 4 and sb["impl"] == 2
+    ka = {(int(t["det"]), int(t["tmpl"]), int(t["sample"])): float(t["snr"]) for t in a}
+    kb = {(int(t["det"]), int(t["tmpl"]), int(t["sample"])): float(t["snr"]) for t in b}
+    common = ka.keys() & kb.keys()
+    assert len(common) >= 0.999 * max(len(ka), len(kb))
+    worst = max(abs(ka[k] - kb[k]) / kb[k] for k in common)
+    assert worst <= SPLIT_RTOL
+    print(f"\nFP16 pairs + split products vs FP32 path: {len(common)} common window peaks of {len(kb)}, "
+          f"max rel SNR diff {worst:.2e}")
+
+
 def test_set_intermediate_argument_checks(lib):
     from paper_2309_00019_gb300 import mf
 
     p = mf.Plan(512.0, 1 << 14, 1, 30.0, 256.0, 5.0, 512)
     with pytest.raises(mf.MFError):
         p.set_intermediate(mf.MF_F16)  # N != 2^20
+    with pytest.raises(mf.MFError):
+        p.set_intermediate(mf.MF_F16X2)
     p.set_intermediate(mf.MF_F32)
     with pytest.raises(mf.MFError):
         p.set_intermediate(mf.MF_BF16)
