@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--small", action="store_true", help="32 s scaled-down workload (quick checks only)")
+    ap.add_argument("--workload", choices=["hierarchy", "uneven"], default="hierarchy",
+                    help="hierarchy (default): the two-stage search step; uneven: 20,000 templates of uneven "
+                         "duration in 4/16/64/256 s length classes over 2 x 4096 s, one fused work queue per pass "
+                         "(--impl reference times the default workload's oracle)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
@@ -259,16 +263,48 @@ def cpu_model():
     return "unknown"
 
 
+def _pool_init_uneven(c, xh, n):
+    _POOL.update(c=c, xh=xh, n=n)
+
+
+def _pool_work_uneven(job):
+    """One worker of the uneven-length workload: from template k0 on (strided over the bank, so every length
+    class is sampled), the oracle's segmented search of the whole stream with one template, both detectors,
+    at the GPU run's segment length; as _pool_work otherwise."""
+    import synth
+    from oracle import mf_oracle as O
+
+    t_go, budget, n_each, k0 = job
+    c, xh, n = _POOL["c"], _POOL["xh"], _POOL["n"]
+    psd = synth.psd_bins(n, c.fs)
+    while time.time() < t_go:
+        time.sleep(0.001)
+    td, k = 0.0, 0
+    while True:
+        i = (k0 + 4099 * k) % len(c.m1)
+        ci = int(c.cls[i])
+        bank = synth.taylorf2(n, c.fs, c.m1[i], c.m2[i], c.f_low)[None, :]
+        O.segmented_filter(xh, c.fs, psd, c.f_low, c.fs / 2, bank, n, int(c.class_len[ci] * c.fs), c.thr, c.window)
+        td += 2 * c.n_samples / c.fs
+        k += 1
+        if (n_each is not None and k >= n_each) or (n_each is None and time.time() - t_go >= budget):
+            break
+    return td, k, time.time()
+
+
 class OraclePool:
     """A spawn-started process pool (safe after the GPU is initialised), one
-    worker per host core, holding the workload's spectra."""
+    worker per host core, holding the workload's inputs (init / work: the
+    workload's initialiser and sample function)."""
 
-    def __init__(self, cfg, workers=None):
+    def __init__(self, cfg, workers=None, init=_pool_init, work=_pool_work, initargs=None):
         import multiprocessing as mp
 
         self.n = workers or host_cores()
-        self.pool = mp.get_context("spawn").Pool(self.n, initializer=_pool_init, initargs=(cfg,))
-        self.pool.map(_pool_work, [(0.0, 0.0, 1, 0)] * self.n)  # workers up, imports and first FFTs done
+        self.work = work
+        self.pool = mp.get_context("spawn").Pool(self.n, initializer=init,
+                                                 initargs=initargs if initargs is not None else (cfg,))
+        self.pool.map(work, [(0.0, 0.0, 1, 0)] * self.n)  # workers up, imports and first FFTs done
         self.k0 = 0
 
     def run(self, budget_s=0.0, n_each=None, slack_s=0.5):
@@ -276,7 +312,7 @@ class OraclePool:
         t_go = time.time() + slack_s
         jobs = [(t_go, budget_s, n_each, self.k0 + 7919 * w) for w in range(self.n)]
         self.k0 += 1
-        res = self.pool.map(_pool_work, jobs)
+        res = self.pool.map(self.work, jobs)
         td = sum(r[0] for r in res)
         el = max(r[2] for r in res) - t_go
         return td / el, sum(r[1] for r in res), el
@@ -341,6 +377,184 @@ def reference_arm(args, rank, world):
     return 0
 
 
+WORKLOAD_UNEVEN = ("uneven-length bank: 20000 TaylorF2 templates (chirp mass 1.2-10, 2PN durations 2.5-91 s from 25 Hz) "
+                   "in 4/16/64/256 s length classes, 2 det x 4096 s @ 2048 Hz in overlapping segments of one "
+                   "autotuned length for all classes, one fused work queue over all classes per pass")
+
+
+def uneven_main(args, rank, world, local):
+    """The uneven-length workload: each step is one pass of mf_batch_run(MF_RUN_FUSED) over the stream (segment
+    spectra, the fused filter's launch pairs over every class's series, trigger compaction); the same JSON
+    line as the default workload.  The fused launch pairs report their CUDA-event times on the first class's
+    plan (mf_profile), which gives the roofline object."""
+    import torch
+
+    import synth
+    from paper_2309_00019_gb300 import _build, mf
+    from paper_2309_00019_gb300.multi import reduce_timing, segment_seed
+
+    if not os.path.exists(mf.LIB_PATH):
+        _build.build()
+    mf.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    c = synth.make_config3(seed=segment_seed(3, rank))
+    x = c.strain(dev)
+    st = torch.cuda.Stream(device=dev)
+    b = mf.Batch(c.fs, 2, c.n_samples, c.f_low, c.fs / 2, c.thr, c.window, c.class_len, stream=st.cuda_stream)
+    b.set_psd(c.psd(c.n_fd), c.n_fd)
+    n_cls = len(c.class_len)
+    n_tmpl = [len(c.class_ids(i)) for i in range(n_cls)]
+    b.autotune(n_tmpl, fused=True)  # set-up, untimed
+    plans = [b.plan(ci) for ci in range(n_cls)]
+    for ci, p in enumerate(plans):
+        ids = c.class_ids(ci)
+        p.bank_reserve(len(ids))
+        p.bank_generate_taylorf2(0, c.m1[ids], c.m2[ids], c.f_low)
+        if args.intermediate != "f32":
+            p.set_intermediate(mf.MF_F16 if args.intermediate == "f16" else mf.MF_F16X2)
+    seg = [b.segment(ci) for ci in range(n_cls)]
+    n = seg[0]["n"]
+    td_step = sum(n_tmpl) * 2 * c.n_samples / c.fs
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    mode = mf.MF_RUN_FUSED
+    for _ in range(max(args.warmup, 0)):
+        b.run(x, mode=mode)
+    torch.cuda.synchronize()
+    for p in plans:
+        p.stats(reset=True)
+    plans[0].profile(True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.zero_()
+            ev[i][0].record(st)
+        b.run(x, mode=mode)
+        with torch.cuda.stream(st):
+            ev[i][1].record(st)
+        plans[0].stats()  # reads this step's launch-pair events (up to 4096 per read)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    sts = [p.stats(reset=True) for p in plans]
+    plans[0].profile(False)
+    t_dev = sum(step_ms) / 1e3
+    td_total = td_step * args.steps
+    if dist is not None:
+        t_max, td_all = reduce_timing(dist, t_dev, td_total, dev)
+    else:
+        t_max, td_all = t_dev, td_total
+    value = td_all / t_max
+
+    hbm_gbs, hbm_kind = peaks()
+    s0 = sts[0]
+    lg = int(round(math.log2(n)))
+    n1s, n2s = 1 << ((lg + 1) // 2), 1 << (lg // 2)
+    names = KERNEL_NAMES.get(s0["impl"], ("pass1", "pass2"))
+    nb = n // 2 + 1
+    roof = None
+    L = s0["pass1_launches"]
+    if L > 0:
+        spl = s0["pass1_series"] / L
+        pair_ms = (s0["pass1_ms"] + s0["pass2_ms"]) / L
+        bps = nb * 8 / 2  # the template's bins, read once for both detectors of a segment
+        alg = spl * bps
+        # the fused launches run the kernels' multi-part instantiations: counters of their own only
+        t1 = measured_traffic(f"{names[0]}_fused<{n1s},{n2s}>", spl)
+        t2 = measured_traffic(f"{names[1]}_fused<{n1s},{n2s}>", spl)
+        roof = {"bound": "hbm", "achieved": alg / (pair_ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": alg / (pair_ms * 1e-3) / 1e9 / hbm_gbs,
+                "traffic": (t1 + t2) if (t1 is not None and t2 is not None) else None,
+                "kernel": f"fused filter {names[0]} + {names[1]} <{n1s},{n2s}> (all classes)",
+                "per_launch_ms": pair_ms, "series_per_launch": spl, "bytes_per_series": bps,
+                "launch_pairs_timed": L, "pass1_ms_per_launch": s0["pass1_ms"] / L,
+                "pass2_ms_per_launch": s0["pass2_ms"] / L,
+                "bytes_convention": "the template's one-sided FD bins, read once and shared by both detectors of a "
+                                    "segment (4,096 B per template-second at 2048 Hz, FP32 bank); time = the two "
+                                    "passes per launch pair (CUDA events around the fused launches)",
+                "peak_kind": f"{hbm_kind} HBM copy bandwidth"}
+    series_step = sum(n_tmpl[ci] * seg[ci]["n_seg"] * 2 for ci in range(n_cls))
+    step_bytes = series_step * nb * 8 / 2
+    step_hbm = step_bytes / (t_dev / args.steps) / 1e9
+
+    e2e = None
+    if not args.no_e2e:  # public API from pinned host strain, triggers read back every step
+        pinned = x.cpu().pin_memory()
+        xd = torch.empty_like(x)
+        te, d2h = [], 0
+        for it in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(st):
+                xd.copy_(pinned, non_blocking=True)
+            b.run(xd, mode=mode)
+            trig, n_found, _ = b.triggers()
+            if it > 0:  # the first pass warms this path up
+                te.append(time.perf_counter() - t0)
+                d2h += trig.nbytes
+        e_val = td_step * args.steps / sum(te)
+        if dist is not None:
+            t_e, td_e_all = reduce_timing(dist, sum(te), td_step * args.steps, dev)
+            e_val = td_e_all / t_e
+        e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(pinned.numel() * 4),
+               "d2h_bytes_per_step": int(d2h / args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        xh = x.cpu().numpy().astype(np.float64)
+        pool = OraclePool(c, init=_pool_init_uneven, work=_pool_work_uneven, initargs=(c, xh, n))
+        try:
+            rate, k, el = pool.run(args.cpu_seconds)
+        finally:
+            pool.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": pool.n, "kind": "oracle",
+               "sample": f"oracle segmented_filter (numpy FP64) in {pool.n} processes, one per host core: {k} "
+                         f"templates spread over the length classes, each over the whole 2 x 4096 s stream in "
+                         f"segments of {n} samples, {el:.1f} s; CPU {cpu_model()}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "f16": "f32 + f16 (f16 intermediate and tensor-core operands)",
+                      "f16x2": "f32 + f16 pairs (hi + lo intermediate and tensor-core operands)"}[args.intermediate],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_UNEVEN, "intermediate": args.intermediate, "segment_n": n,
+                       "segments_per_class": [g["n_seg"] for g in seg], "templates_per_class": n_tmpl,
+                       "series_per_step": series_step, "td_seconds_per_step": td_step,
+                       "l2": "512 MB buffer written between timed steps; banks (84 GB) streamed from HBM",
+                       "run_mode": "MF_RUN_FUSED", "parallelism": f"{world} independent streams (one per GPU)"},
+            "roofline": roof,
+            "hbm_step": {"template_bytes_per_step": step_bytes, "achieved_gbs": step_hbm, "peak_gbs": hbm_gbs,
+                         "frac": step_hbm / hbm_gbs, "peak_kind": hbm_kind},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(sum(s_["launches"] for s_ in sts)),
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.kernel_case:
@@ -348,6 +562,8 @@ def main():
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "uneven":
+        return uneven_main(args, rank, world, local)
 
     import torch
 

@@ -275,7 +275,8 @@ mf_status mf_device_triggers(mf_plan_t plan, const mf_trigger** trig, const int6
 
 /* Counters of one plan.  launches: kernels this plan enqueued.  When profiling
  * is on, CUDA events bracket the two filter kernels of each template batch on
- * the plan's stream (up to 1024 batches between reads): pass1_* is the
+ * the plan's stream (up to 4096 batches between reads; a batch runner's fused
+ * launch pairs are reported by its first class's plan): pass1_* is the
  * product + column-transform kernel, pass2_* the row-transform + SNR /
  * threshold / window-max kernel; *_series = (template, detector) series they
  * processed, *_ms = summed device time. */

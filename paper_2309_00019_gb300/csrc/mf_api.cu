@@ -124,7 +124,7 @@ bool plan_capturable(const mf_plan_s* p) {
 }  // namespace mf
 
 namespace {
-constexpr int kProfBatches = 1024;
+constexpr int kProfBatches = 4096;  // launch pairs timed between two reads of the counters
 
 // counts the kernels a block of code launches into p->stats.launches
 struct LaunchScope {
@@ -1141,8 +1141,15 @@ int filter_fused(mf_plan_s* const* plans, const void* const* dtilde, const int64
     ps.n_series = (int)ser;
     a.first_batch = first ? 1 : 0;
     first = false;
-    if ((e = launch_filter2_fused(a, ps, scratch_map, st)) != cudaSuccess)
+    const bool prof = p0->prof && (int)p0->samples.size() < kProfBatches;
+    const int e0 = prof ? (int)p0->samples.size() * 3 : 0;
+    if (prof) cudaEventRecord(p0->ev[e0], st);
+    if ((e = launch_filter2_fused(a, ps, scratch_map, st, prof ? p0->ev[e0 + 1] : nullptr)) != cudaSuccess)
       return bad(MF_ECUDA, std::string("fused filter launch: ") + cudaGetErrorString(e));
+    if (prof) {
+      cudaEventRecord(p0->ev[e0 + 2], st);
+      p0->samples.push_back({e0, ser});
+    }
   }
   for (int j = 0; j < n_plans; ++j) {
     mf_plan_s* p = plans[j];

@@ -724,9 +724,11 @@ cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& tm, cud
   return pass2_parts(a, kOnePlan, tm, st);
 }
 
-cudaError_t launch_filter2_fused(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st) {
+cudaError_t launch_filter2_fused(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& tm, cudaStream_t st,
+                                 cudaEvent_t between) {
   if (ps.n < 1 || ps.n > kMaxParts || ps.n_series < 1) return cudaErrorInvalidValue;
   cudaError_t e = pass1_parts(a, ps, st);
+  if (e == cudaSuccess && between) e = cudaEventRecord(between, st);
   if (e == cudaSuccess) e = pass2_parts(a, ps, tm, st);
   return e;
 }

@@ -131,7 +131,8 @@ int plan_batch(const ::mf_plan_s* p);
 // scratch_series series across plan boundaries.  The plans share N, the window and the
 // intermediate, with an FP32 bank and FP32 data; `scratch` holds scratch_series series of the
 // intermediate (N x 8 bytes each; scratch_map encoded for it) and every step runs on st.  A wait
-// that times out is reported by plans[0].  On failure *err holds the message.
+// that times out is reported by plans[0], and so are the launch counts and, when plans[0] is
+// profiling (mf_profile), the launch pairs' CUDA-event times.  On failure *err holds the message.
 int filter_fused(::mf_plan_s* const* plans, const void* const* dtilde, const int64_t* ld, int n_plans, void* scratch,
                  int64_t scratch_series, const CUtensorMap& scratch_map, cudaStream_t st, std::string* err);
 // The TMA-staged filter passes (mf_filter.cu).  The bank rows and the
@@ -143,9 +144,10 @@ cudaError_t launch_filter2_pass2(const FilterArgs& a, const CUtensorMap& scratch
 cudaError_t launch_filter2_pass2_tc(const FilterArgs& a, cudaStream_t st, const FilterParts* parts = nullptr);
 // Both passes over the series of several plans' parts in one launch each (ps.n >= 1): the
 // per-part fields come from ps, the rest (geometry, types, window, scratch, tables, status)
-// from a; the scratch holds ps.n_series series (scratch_map encoded for at least as many).
+// from a; the scratch holds ps.n_series series (scratch_map encoded for at least as many).  `between`
+// (optional) is recorded on st between the two launches.
 cudaError_t launch_filter2_fused(const FilterArgs& a, const FilterParts& ps, const CUtensorMap& scratch_map,
-                                 cudaStream_t st);
+                                 cudaStream_t st, cudaEvent_t between = nullptr);
 // Tensor map of the pass-1 -> pass-2 scratch (`series` series of length n)
 // through which pass 2 reads its items; all zero where pass 2 needs none.
 cudaError_t encode_scratch_map(int64_t n, const float2* scratch, int64_t series, CUtensorMap* m);
