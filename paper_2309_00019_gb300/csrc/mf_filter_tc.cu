@@ -36,10 +36,12 @@ namespace mf {
 
 namespace {
 
-constexpr int kGroup = 128;                       // threads of one consumer group
-constexpr int kGroups = 4;
+constexpr int kGroupWarps = 8;                    // warps of one consumer group: 4 per operand tile
+constexpr int kGroup = kGroupWarps * 32;          // threads of one consumer group
+constexpr int kGroups = 3;
+constexpr int kBufs = 4;                          // tensor-memory buffers: items from stage 1 to the epilogue
 constexpr int kTcThreads = kGroups * kGroup + 64; // + producer warp + MMA warp
-constexpr int kProdWarp = kGroups * 4, kMmaWarp = kProdWarp + 1;
+constexpr int kProdWarp = kGroups * kGroupWarps, kMmaWarp = kProdWarp + 1;
 constexpr int kTcRows = kPanel16;                 // rows per item
 constexpr int kTcK = 64;                          // 32 complex values, real and imaginary interleaved
 constexpr int kLbo = 128, kSbo = 1024;            // unpadded core-matrix layouts
@@ -47,7 +49,7 @@ constexpr int kTileBytes = 128 * kTcK * 2;        // one M = 128 operand tile, 1
 constexpr int kBBytes = 64 * kTcK * 2;            // one image of the DFT matrix B (64 x 64), 8 KB
 constexpr int kTwStride = 33;                     // padded rows of the w1024^{q u} table (float2)
 constexpr uint32_t kBufCols = 128;                // 2 tiles x 64 FP32 columns
-constexpr uint32_t kTmemCols = kGroups * kBufCols;  // all 512
+constexpr uint32_t kTmemCols = kBufs * kBufCols;  // all 512
 constexpr uint32_t kIdesc2 = tc_idesc_f16(128, 64);          // A K-major (stage 2)
 constexpr uint32_t kIdesc1 = kIdesc2 | (1u << 15);           // A MN-major (stage 1)
 
@@ -63,7 +65,7 @@ struct TcGeo {
   static constexpr int B_OFF = SLOTS * ITEM;
   static constexpr int TW_OFF = B_OFF + IMG * kBBytes;
   static constexpr int BAR_OFF = TW_OFF + 32 * kTwStride * 8;
-  static constexpr int NBAR = 3 * SLOTS + 3 * kGroups + 1;
+  static constexpr int NBAR = 3 * SLOTS + 3 * kBufs + 1;
   static constexpr int SMEM = BAR_OFF + NBAR * 8 + 16;
   static_assert(SMEM <= 232448, "k_rows_tc shared memory");
 };
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + G::BAR_OFF);  // [kSlots]
   uint64_t* a2full = full + kSlots;                              // [kSlots]
   uint64_t* empty = a2full + kSlots;                             // [kSlots]
-  uint64_t* d1 = empty + kSlots;                                 // [kGroups]
-  uint64_t* d2 = d1 + kGroups;
-  uint64_t* tfree = d2 + kGroups;
-  uint64_t* drain = tfree + kGroups;
+  uint64_t* d1 = empty + kSlots;                                 // [kBufs]
+  uint64_t* d2 = d1 + kBufs;
+  uint64_t* tfree = d2 + kBufs;
+  uint64_t* drain = tfree + kBufs;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::BAR_OFF + G::NBAR * 8);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
   const int n_series = MP ? ps.n_series : a.count * a.n_det;
@@ -141,10 +143,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
       mbar_init(a2full + i, kGroup);
       mbar_init(empty + i, 1);
     }
-    for (int g = 0; g < kGroups; ++g) {
-      mbar_init(d1 + g, 1);
-      mbar_init(d2 + g, 1);
-      mbar_init(tfree + g, kGroup);
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(d1 + b, 1);
+      mbar_init(d2 + b, 1);
+      mbar_init(tfree + b, kGroup);
     }
     mbar_init(drain, 1);
     fence_mbar_init();
@@ -187,22 +189,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
       while (n2 < n_mine) {
         bool progress = false;
         if (n1 < n_mine) {
-          const int slot = n1 % kSlots, g = n1 % kGroups;
+          const int slot = n1 % kSlots, b = n1 % kBufs;
           if (mbar_test_wait(full + slot, par(n1 / kSlots)) &&
-              (n1 < kGroups || mbar_test_wait(tfree + g, par(n1 / kGroups - 1)))) {
+              (n1 < kBufs || mbar_test_wait(tfree + b, par(n1 / kBufs - 1)))) {
             tc_fence_after();
-            stage_mmas<SPLIT>(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
-            tc_commit(d1 + g);
+            stage_mmas<SPLIT>(tmem + b * kBufCols, smem_u32(sm + slot * kItemBytes), true, bb);
+            tc_commit(d1 + b);
             ++n1;
             progress = true;
           }
         }
         if (n2 < n1) {
-          const int slot = n2 % kSlots, g = n2 % kGroups;
+          const int slot = n2 % kSlots, b = n2 % kBufs;
           if (mbar_test_wait(a2full + slot, par(n2 / kSlots))) {
             tc_fence_after();
-            stage_mmas<SPLIT>(tmem + g * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
-            tc_commit(d2 + g);
+            stage_mmas<SPLIT>(tmem + b * kBufCols, smem_u32(sm + slot * kItemBytes), false, bb);
+            tc_commit(d2 + b);
             tc_commit(empty + slot);
             ++n2;
             progress = true;
@@ -222,15 +224,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
       }
     }
   } else {
-    // ---- consumer group g = warp / 4: items k = g, g + 4, ...; twiddle, then epilogue ----
-    const int g = warp >> 2, lt = tid & (kGroup - 1);
-    const int r = lt & 7, qg = lt >> 3;
-    const uint32_t tbuf = tmem + g * kBufCols + ((uint32_t)(32 * (warp & 3)) << 16);
-    RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, nullptr, a.pos0, a.n_det, a.window, a.valid_begin, a.valid_end,
-              a.n_win, a.n_sel_total, a.slots, a.row_valid};
+    // ---- consumer group g = warp / 8: items k = g, g + 3, ... in buffer k % 4; twiddle, then epilogue ----
+    // warps 4 h .. 4 h + 3 of a group own tile h; thread = TMEM lane row of that tile in both stages
+    const int g = warp / kGroupWarps, wg = warp % kGroupWarps, h = wg >> 2;
+    const int row = 32 * (wg & 3) + lane;
+    const int r = row & 7, qg = row >> 3;
+    const int q = qg + 16 * h;  // stage-1 row (q, r) of tile h, then stage-2 row (u = q, r)
+    const float2* twq = tw + q * kTwStride;
     for (int k = g; k < n_mine; k += kGroups) {
-      const int slot = k % kSlots;
+      // the epilogue's fields are kernel parameters, read where used (no registers held across the loop)
+      const RawEpi ep{a.sel, a.inv_sigma, a.thr_raw, nullptr, a.pos0, a.n_det, a.window, a.valid_begin,
+                      a.valid_end, a.n_win, a.n_sel_total, a.slots, a.row_valid};
+      const int slot = k % kSlots, b = k % kBufs;
       unsigned char* sl = sm + slot * kItemBytes;
+      const uint32_t tbuf = tmem + b * kBufCols + 64 * h + ((uint32_t)(32 * (wg & 3)) << 16);
       // the item's series state first: its dependent global loads overlap the waits below
       const int item = blockIdx.x + k * gridDim.x;
       const int s = n_series - 1 - item / NP;
@@ -246,27 +253,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
         se = ep.series(s);
         sc = series_scale16(__ldg(a.inv_sigma + a.sel[a.pos0 + s / a.n_det]));
       }
-      se.ratio /= sc;  // exact: sc is a power of two
-      se.thr *= sc * sc;
       const int64_t j1 = (int64_t)(item % NP) * kTcRows + r;
       // twiddle w1024^{q u}, round to FP16, stage-2 operand row (u, r), K = (q, c), over the slot
       // (warp-uniform outcome: the tensor-memory loads below are warp-collective)
-      if (!__all_sync(0xffffffffu, mbar_wait_at(d1 + g, par(k / kGroups), a.status, 14, k))) break;
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d1 + b, par(k / kBufs), a.status, 14, k))) break;
       tc_fence_after();
-      // eight chunks of 16 columns (tile h = t / 4, u = 8 (t % 4) .. + 7); chunk t + 1 loads while t is used
+      // four chunks of 16 columns (u = 8 t .. 8 t + 7); chunk t + 1 loads while t is used
       float ya[16], yb[16];
       tmem_ld16_issue(tbuf, ya);
       tmem_wait(ya);
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
+      for (int t = 0; t < 4; ++t) {
         float(&cur)[16] = (t & 1) ? yb : ya;
         float(&nxt)[16] = (t & 1) ? ya : yb;
-        if (t + 1 < 8) tmem_ld16_issue(tbuf + 64 * ((t + 1) >> 2) + 16 * ((t + 1) & 3), nxt);
-        const int q = qg + 16 * (t >> 2);
-        const float2* twq = tw + q * kTwStride;
+        if (t + 1 < 4) tmem_ld16_issue(tbuf + 16 * (t + 1), nxt);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int u = 8 * (t & 3) + i;
+          const int u = 8 * t + i;
           const float2 z = cmul(make_float2(cur[2 * i], cur[2 * i + 1]), twq[u]);
           const int off = cm_offset(u * 8 + r, 2 * q, kLbo, kSbo);
           const __half2 hi = __floats2half2_rn(z.x, z.y);
@@ -276,34 +279,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_rows_tc(FilterArgs a, const _
             *reinterpret_cast<__half2*>(sl + 2 * kTileBytes + off) = __floats2half2_rn(z.x - hf.x, z.y - hf.y);
           }
         }
-        if (t + 1 < 8) tmem_wait(nxt);
+        if (t + 1 < 4) tmem_wait(nxt);
       }
       fence_proxy_async();  // our operand writes before the MMAs that read them
       mbar_arrive(a2full + slot);
-      // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r
-      if (!__all_sync(0xffffffffu, mbar_wait_at(d2 + g, par(k / kGroups), a.status, 15, k))) break;
+      // the series state is used from here on (its loads were issued before the stage-1 wait)
+      se.ratio /= sc;  // exact: sc is a power of two
+      se.thr *= sc * sc;
+      // epilogue: row (u, r) of tile h holds z[u + 32 v], v = 0..31, of row j1 = 8 panel + r (u = q)
+      if (!__all_sync(0xffffffffu, mbar_wait_at(d2 + b, par(k / kBufs), a.status, 15, k))) break;
       tc_fence_after();
       float za[16], zb[16];
       tmem_ld16_issue(tbuf, za);
       tmem_wait(za);
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {  // tile h = t / 4, v = 8 (t % 4) .. + 7
+      for (int t = 0; t < 4; ++t) {  // v = 8 t .. 8 t + 7
         float(&cur)[16] = (t & 1) ? zb : za;
         float(&nxt)[16] = (t & 1) ? za : zb;
-        if (t + 1 < 8) tmem_ld16_issue(tbuf + 64 * ((t + 1) >> 2) + 16 * ((t + 1) & 3), nxt);
-        const int u = qg + 16 * (t >> 2);
+        if (t + 1 < 4) tmem_ld16_issue(tbuf + 16 * (t + 1), nxt);
         float mx = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fmaf(cur[2 * i], cur[2 * i], cur[2 * i + 1] * cur[2 * i + 1]));
         if (mx >= se.thr) {  // rare: some sample of this row is over the threshold
 #pragma unroll
           for (int i = 0; i < 8; ++i)
-            ep(se, j1 + (int64_t)N1 * (u + 32 * (8 * (t & 3) + i)), make_float2(cur[2 * i], cur[2 * i + 1]));
+            ep(se, j1 + (int64_t)N1 * (q + 32 * (8 * t + i)), make_float2(cur[2 * i], cur[2 * i + 1]));
         }
-        if (t + 1 < 8) tmem_wait(nxt);
+        if (t + 1 < 4) tmem_wait(nxt);
       }
       tc_fence_before();  // our tensor-memory reads before the MMAs that reuse the buffer
-      mbar_arrive(tfree + g);
+      mbar_arrive(tfree + b);
     }
   }
   tc_fence_before();
