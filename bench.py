@@ -377,9 +377,9 @@ def reference_arm(args, rank, world):
     return 0
 
 
-WORKLOAD_UNEVEN = ("uneven-length bank: 20000 TaylorF2 templates (chirp mass 1.2-10, 2PN durations 2.5-91 s from 25 Hz) "
-                   "in 4/16/64/256 s length classes, 2 det x 4096 s @ 2048 Hz in overlapping segments of one "
-                   "autotuned length for all classes, one fused work queue over all classes per pass")
+WORKLOAD_UNEVEN = ("uneven-length bank: 20000 TaylorF2 templates (chirp mass 1.2-10, 2PN durations 2.5-91 s "
+                   "from 25 Hz) in 4/16/64/256 s length classes, 2 det x 4096 s @ 2048 Hz in overlapping segments "
+                   "of one autotuned length for all classes, one fused work queue over all classes per pass")
 
 
 def uneven_main(args, rank, world, local):

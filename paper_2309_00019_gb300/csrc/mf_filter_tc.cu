@@ -15,19 +15,20 @@
 // stage-1 result times w1024^{q u}, rounded to FP16 (K-major).  M = 256 rows
 // per stage, as two M = 128 tiles.
 //
-// One persistent CTA per SM, 576 threads.  Warp 16 copies items into six
-// shared-memory slots; a slot holds its item's stage-1 operand and then (written
-// over it) its stage-2 operand, and is free again once stage 2 has read it.
-// Warp 17 owns all 512 tensor-memory columns (four buffers of 2 x 64) and one
-// lane issues the MMAs in an event loop: stage 1 of item k when its slot has
-// landed and its buffer is free, stage 2 when its operand is written, in item
-// order each.  Warps 0-15 are four consumer groups; group g takes items
-// k = g, g + 4, ... in buffer g.  In a group, thread t = TMEM lane t of both
-// tiles (q or u = t / 8 + 16 h, r = t % 8 for tile h) applies the twiddles
-// between the stages and runs the epilogue (raw |z|^2 against the
-// per-template threshold, window maxima) on the stage-2 accumulators.
-// Barriers: per slot full / a2full / empty, per buffer d1 / d2 / tfree, and
-// a drain barrier; every wait is bounded.
+// One persistent CTA per SM, 832 threads.  Warp 24 copies items into six
+// shared-memory slots (three with FP16 pairs); a slot holds its item's stage-1
+// operand and then (written over it) its stage-2 operand, and is free again
+// once stage 2 has read it.  Warp 25 owns all 512 tensor-memory columns (four
+// buffers of 2 x 64) and one lane issues the MMAs in an event loop: stage 1 of
+// item k into buffer k % 4 when its slot has landed and the buffer is free,
+// stage 2 when its operand is written, in item order each.  Warps 0-23 are
+// three consumer groups of eight warps; group g takes items k = g, g + 3, ...,
+// so one buffer's stage 1 can complete while every group is busy.  In a group,
+// warps 4 h .. 4 h + 3 own tile h, and thread t = TMEM lane t of that tile
+// (q or u = t / 8 + 16 h, r = t % 8) applies the twiddles between the stages
+// and runs the epilogue (raw |z|^2 against the per-template threshold, window
+// maxima) on the stage-2 accumulators.  Barriers: per slot full / a2full /
+// empty, per buffer d1 / d2 / tfree, and a drain barrier; every wait is bounded.
 #include "mf_common.cuh"
 #include "mf_tc.cuh"
 #include "mf_tma.cuh"
