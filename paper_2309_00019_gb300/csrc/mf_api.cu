@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -968,20 +969,51 @@ mf_status mf_get_coincs(mf_plan_t p, mf_coinc* out, int64_t cap, int64_t* n_foun
   if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_coincs count");
   *n_found = (int64_t)n;
   const int64_t have = std::min<int64_t>((int64_t)n, p->coinc_cap);
-  std::vector<mf_coinc> all(have);
-  if (have > 0) {
-    e = cudaMemcpyAsync(all.data(), p->coincs, have * sizeof(mf_coinc), cudaMemcpyDeviceToHost, p->st);
+  const int64_t m = std::min<int64_t>(have, cap);
+  if (m > 0) {  // a count-only call (cap 0) copies nothing
+    std::unique_ptr<mf_coinc[]> rec(new mf_coinc[have]);
+    e = cudaMemcpyAsync(rec.get(), p->coincs, have * sizeof(mf_coinc), cudaMemcpyDeviceToHost, p->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) return cuda_fail(p, e, "mf_get_coincs copy");
+    // order by (tmpl, shift, sample0, sample1) through packed keys: tmpl and shift are non-negative int32;
+    // the samples are compared as int64 (sign bit flipped, so that unsigned order is signed order)
+    struct Key {
+      uint64_t ts, s0, s1;
+      int64_t i;
+    };
+    std::vector<Key> key((size_t)have);
+    for (int64_t i = 0; i < have; ++i) {
+      const mf_coinc& c = rec[i];
+      key[(size_t)i] = Key{((uint64_t)(uint32_t)c.tmpl << 32) | (uint32_t)c.shift,
+                           (uint64_t)c.sample0 ^ (uint64_t(1) << 63), (uint64_t)c.sample1 ^ (uint64_t(1) << 63), i};
+    }
+    auto less = [](const Key& a, const Key& b) {
+      if (a.ts != b.ts) return a.ts < b.ts;
+      if (a.s0 != b.s0) return a.s0 < b.s0;
+      return a.s1 < b.s1;
+    };
+    // counting sort by template id (ids are < n_tmpl), then each template's few records by the rest of the key
+    std::vector<int64_t> start((size_t)p->n_tmpl + 1, 0);
+    bool ids_ok = true;
+    for (int64_t i = 0; i < have && ids_ok; ++i) {
+      const int32_t t = rec[i].tmpl;
+      if (t < 0 || t >= p->n_tmpl) ids_ok = false;
+      else ++start[(size_t)t + 1];
+    }
+    if (ids_ok) {
+      for (int64_t t = 0; t < p->n_tmpl; ++t) start[(size_t)t + 1] += start[(size_t)t];
+      std::vector<Key> by((size_t)have);
+      std::vector<int64_t> pos(start.begin(), start.end() - 1);
+      for (int64_t i = 0; i < have; ++i) by[(size_t)pos[(size_t)rec[i].tmpl]++] = key[(size_t)i];
+      for (int64_t t = 0; t < p->n_tmpl; ++t)
+        if (start[(size_t)t + 1] - start[(size_t)t] > 1)
+          std::sort(by.begin() + start[(size_t)t], by.begin() + start[(size_t)t + 1], less);
+      key.swap(by);
+    } else {
+      std::sort(key.begin(), key.end(), less);
+    }
+    for (int64_t j = 0; j < m; ++j) out[j] = rec[key[(size_t)j].i];
   }
-  std::sort(all.begin(), all.end(), [](const mf_coinc& a, const mf_coinc& b) {
-    if (a.tmpl != b.tmpl) return a.tmpl < b.tmpl;
-    if (a.shift != b.shift) return a.shift < b.shift;
-    if (a.sample0 != b.sample0) return a.sample0 < b.sample0;
-    return a.sample1 < b.sample1;
-  });
-  const int64_t m = std::min<int64_t>(have, cap);
-  if (m > 0) std::memcpy(out, all.data(), m * sizeof(mf_coinc));
   if ((int64_t)n > cap || (int64_t)n > p->coinc_cap)
     return fail(p, MF_EOVERFLOW, "mf_get_coincs: " + std::to_string(n) + " coincidences exceed the buffer");
   return MF_OK;

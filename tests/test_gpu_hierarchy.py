@@ -48,6 +48,12 @@ def test_coincidences_followup_and_union(small_run):
     want_keys = [(int(x["tmpl"]), int(x["shift"]), int(x["sample0"]), int(x["sample1"])) for x in want]
     assert got_keys == want_keys and nco > 0
     assert np.allclose(co["rho_c"], want["rho_c"], rtol=1e-4)
+    # a read into a smaller buffer: the first records of the same order, and the overflow status
+    from paper_2309_00019_gb300 import mf
+    if nco > 3:
+        co3, n3, st3 = h.p1.coincs(cap=3)
+        assert n3 == nco and st3 == mf.MF_EOVERFLOW
+        assert [(int(x["tmpl"]), int(x["shift"]), int(x["sample0"]), int(x["sample1"])) for x in co3] == got_keys[:3]
     assert np.any(co["shift"] == 0) and np.any(co["shift"] > 0)  # zero-lag and time-shifted follow-ups
     followed = np.nonzero(h.followed.cpu().numpy())[0]
     assert list(followed) == list(ref["followed"])
