@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -970,7 +971,7 @@ mf_status mf_get_coincs(mf_plan_t p, mf_coinc* out, int64_t cap, int64_t* n_foun
   *n_found = (int64_t)n;
   const int64_t have = std::min<int64_t>((int64_t)n, p->coinc_cap);
   const int64_t m = std::min<int64_t>(have, cap);
-  if (m > 0) {  // a count-only call (cap 0) copies nothing
+  if (m > 0) try {  // a count-only call (cap 0) copies nothing; no allocation failure crosses the ABI
     std::unique_ptr<mf_coinc[]> rec(new mf_coinc[have]);
     e = cudaMemcpyAsync(rec.get(), p->coincs, have * sizeof(mf_coinc), cudaMemcpyDeviceToHost, p->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
@@ -1013,6 +1014,8 @@ mf_status mf_get_coincs(mf_plan_t p, mf_coinc* out, int64_t cap, int64_t* n_foun
       std::sort(key.begin(), key.end(), less);
     }
     for (int64_t j = 0; j < m; ++j) out[j] = rec[key[(size_t)j].i];
+  } catch (const std::bad_alloc&) {
+    return fail(p, MF_ENOMEM, "mf_get_coincs: host memory for " + std::to_string(have) + " records");
   }
   if ((int64_t)n > cap || (int64_t)n > p->coinc_cap)
     return fail(p, MF_EOVERFLOW, "mf_get_coincs: " + std::to_string(n) + " coincidences exceed the buffer");

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -626,46 +627,50 @@ mf_status mf_batch_run(mf_batch_t b, const float* strain, int64_t ld, int32_t mo
 }
 
 mf_status mf_batch_get_triggers(mf_batch_t b, mf_batch_trigger* out, int64_t cap, int64_t* n_found) {
-  if (!b || !n_found || (cap > 0 && !out)) return bfail(b, MF_EINVAL, "mf_batch_get_triggers: null argument");
-  if (!b->ran) return bfail(b, MF_ESTATE, "mf_batch_get_triggers: no run");
-  cudaError_t e = cudaStreamSynchronize(b->main);
-  if (e != cudaSuccess) return bcuda(b, e, "mf_batch_get_triggers sync");
-  std::vector<mf_batch_trigger> all;
-  bool overflow = false;
-  for (int ci = 0; ci < b->d.n_class; ++ci) {
-    mf_batch_s::Cls& c = b->cls[ci];
-    if (!has_bank(c)) continue;
-    int64_t n = 0;
-    mf_status s = mf_get_triggers(c.plan, nullptr, 0, &n);
-    if (s != MF_OK && s != MF_EOVERFLOW) return bplan(b, c.plan, s, "mf_batch_get_triggers");
-    std::vector<mf_trigger> t((size_t)std::min<int64_t>(n, b->d.max_triggers));
-    s = mf_get_triggers(c.plan, t.data(), (int64_t)t.size(), &n);
-    if (s == MF_EOVERFLOW) overflow = true;
-    else if (s != MF_OK) return bplan(b, c.plan, s, "mf_batch_get_triggers");
-    for (const mf_trigger& x : t) {
-      const int64_t seg = x.det / b->d.n_det;
-      mf_batch_trigger y{};
-      y.det = (int32_t)(x.det - seg * b->d.n_det);
-      y.cls = ci;
-      y.tmpl = x.tmpl;
-      y.sample = seg * c.stride + x.sample;
-      y.snr = x.snr;
-      y.phase = x.phase;
-      all.push_back(y);
+  try {  // the host lists can be large: no allocation failure crosses the ABI
+    if (!b || !n_found || (cap > 0 && !out)) return bfail(b, MF_EINVAL, "mf_batch_get_triggers: null argument");
+    if (!b->ran) return bfail(b, MF_ESTATE, "mf_batch_get_triggers: no run");
+    cudaError_t e = cudaStreamSynchronize(b->main);
+    if (e != cudaSuccess) return bcuda(b, e, "mf_batch_get_triggers sync");
+    std::vector<mf_batch_trigger> all;
+    bool overflow = false;
+    for (int ci = 0; ci < b->d.n_class; ++ci) {
+      mf_batch_s::Cls& c = b->cls[ci];
+      if (!has_bank(c)) continue;
+      int64_t n = 0;
+      mf_status s = mf_get_triggers(c.plan, nullptr, 0, &n);
+      if (s != MF_OK && s != MF_EOVERFLOW) return bplan(b, c.plan, s, "mf_batch_get_triggers");
+      std::vector<mf_trigger> t((size_t)std::min<int64_t>(n, b->d.max_triggers));
+      s = mf_get_triggers(c.plan, t.data(), (int64_t)t.size(), &n);
+      if (s == MF_EOVERFLOW) overflow = true;
+      else if (s != MF_OK) return bplan(b, c.plan, s, "mf_batch_get_triggers");
+      for (const mf_trigger& x : t) {
+        const int64_t seg = x.det / b->d.n_det;
+        mf_batch_trigger y{};
+        y.det = (int32_t)(x.det - seg * b->d.n_det);
+        y.cls = ci;
+        y.tmpl = x.tmpl;
+        y.sample = seg * c.stride + x.sample;
+        y.snr = x.snr;
+        y.phase = x.phase;
+        all.push_back(y);
+      }
     }
+    std::sort(all.begin(), all.end(), [](const mf_batch_trigger& a, const mf_batch_trigger& c) {
+      if (a.cls != c.cls) return a.cls < c.cls;
+      if (a.det != c.det) return a.det < c.det;
+      if (a.tmpl != c.tmpl) return a.tmpl < c.tmpl;
+      return a.sample < c.sample;
+    });
+    *n_found = (int64_t)all.size();
+    const int64_t m = std::min<int64_t>(cap, (int64_t)all.size());
+    if (m > 0) std::copy(all.begin(), all.begin() + m, out);
+    if (overflow || (int64_t)all.size() > cap)
+      return bfail(b, MF_EOVERFLOW, "mf_batch_get_triggers: triggers exceed a buffer");
+    return MF_OK;
+  } catch (const std::bad_alloc&) {
+    return bfail(b, MF_ENOMEM, "mf_batch_get_triggers: host memory");
   }
-  std::sort(all.begin(), all.end(), [](const mf_batch_trigger& a, const mf_batch_trigger& c) {
-    if (a.cls != c.cls) return a.cls < c.cls;
-    if (a.det != c.det) return a.det < c.det;
-    if (a.tmpl != c.tmpl) return a.tmpl < c.tmpl;
-    return a.sample < c.sample;
-  });
-  *n_found = (int64_t)all.size();
-  const int64_t m = std::min<int64_t>(cap, (int64_t)all.size());
-  if (m > 0) std::copy(all.begin(), all.begin() + m, out);
-  if (overflow || (int64_t)all.size() > cap)
-    return bfail(b, MF_EOVERFLOW, "mf_batch_get_triggers: triggers exceed a buffer");
-  return MF_OK;
 }
 
 }  // extern "C"

@@ -508,7 +508,8 @@ class Batch:
 
     def run(self, strain, ld=None, mode=None):
         """mf_batch_run; mode None: the fused work queue under a captured graph (MF_RUN_FUSED_GRAPH) when every
-        class with a plan has the same segment length, else the classes one after another (MF_RUN_SERIAL)."""
+        class with a plan has the same segment length (the fused queue also needs FP32 banks and data), else the
+        classes one after another (MF_RUN_SERIAL)."""
         ld = strain.shape[-1] if ld is None else ld
         if mode is None:
             ns = {self.segment(ci)["n"] for ci in range(self.n_class)} - {0}
