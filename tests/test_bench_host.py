@@ -1,12 +1,14 @@
 """CPU checks of bench.py's host logic: the DRAM-traffic lookup in the committed
-profile summaries, and the reference arm's JSON line (the oracle timed on the
-host) with the keys of the bench contract."""
+profile summaries, the reference arm's JSON line (the oracle timed on the
+host) with the keys of the bench contract, and the uneven-length workload's
+oracle worker."""
 
 import contextlib
 import io
 import json
 import types
 
+import numpy as np
 import pytest
 
 import bench
@@ -41,3 +43,19 @@ def test_reference_arm_prints_one_contract_line():
     with contextlib.redirect_stdout(buf):
         assert bench.reference_arm(args, 1, 2) == 0
     assert buf.getvalue() == ""
+
+
+def test_uneven_oracle_worker_filters_one_template_over_the_stream():
+    import synth
+
+    c = synth.make_config3(seed=2, n_tmpl=6, T=256.0, fs=256.0, f_low=40.0, class_len=(2.0, 8.0), n_inj=1)
+    rng = np.random.default_rng(0)
+    strain = rng.standard_normal((2, c.n_samples))
+    bench._pool_init_uneven(c, strain, 4096)
+    td, k, _ = bench._pool_work_uneven((0.0, 0.0, 1, 3))
+    assert k == 1 and td == pytest.approx(2 * c.n_samples / c.fs)
+
+
+def test_fused_kernels_have_no_traffic_until_captured():
+    assert bench.measured_traffic("k_cols_h16_fused<1024,1024>", 128) is None
+    assert bench.measured_traffic("k_rows_tc_fused<1024,1024>", 128) is None

@@ -145,6 +145,26 @@ def test_autotune_picks_admissible_segments(mf):
         compare_lists(trig[trig["cls"] == ci], ref, c.thr, c.window)
 
 
+def test_autotune_fused_picks_one_length_and_runs_fused(mf):
+    """The common-N autotuner gives every class with templates the same admissible segment length; at it the
+    fused graph and the serial per-class run agree bit for bit."""
+    c = _small()
+    x = c.strain(DEV)
+    st = torch.cuda.Stream()
+    b = _batch(mf, c, stream=st.cuda_stream)
+    n_tmpl = [len(c.class_ids(i)) for i in range(3)]
+    b.autotune(n_tmpl, fused=True)
+    seg = [b.segment(ci) for ci in range(3)]
+    assert len({g["n"] for g, k in zip(seg, n_tmpl) if k > 0}) == 1
+    for g in seg:
+        assert g["stride"] > 0 and g["tmpl_len"] + g["stride"] <= g["n"] and g["est_ms"] > 0
+    _load_banks(b, c)
+    b.run(x, mode=mf.MF_RUN_SERIAL)
+    ref = b.triggers()[0]
+    b.run(x)  # default: the fused graph, since the classes share N
+    assert np.array_equal(b.triggers()[0], ref) and len(ref) > 0
+
+
 def test_config3_uneven_lengths_full_size(mf):
     """20,000 templates, 2 x 4096 s at 2048 Hz: autotuned segment lengths, the
     three run modes timed, and 2 templates per class checked by the oracle's
