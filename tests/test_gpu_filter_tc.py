@@ -193,3 +193,25 @@ def test_set_intermediate_argument_checks(lib):
     with pytest.raises(mf.MFError):
         p.set_intermediate(mf.MF_BF16)
     p.close()
+
+
+def test_tc_empty_subset_and_small_trigger_buffer(case):
+    """Both FP16 intermediates: a call that selects no template gives no trigger, and a trigger buffer smaller
+    than the count returns its first records with the full count and MF_EOVERFLOW."""
+    from paper_2309_00019_gb300 import mf
+
+    d = torch.from_numpy(case["fd"]).to(DEV)
+    for inter in (mf.MF_F16, mf.MF_F16X2):
+        p = mf.Plan(FS, N, 2, F_LOW, FS / 2, 4.0, int(FS), max_triggers=1 << 20)
+        p.set_psd(case["psd"])
+        p.load_bank(case["bank"])
+        p.set_intermediate(inter)
+        p.filter(d, subset=torch.zeros(0, dtype=torch.int32, device=DEV), n_subset=0)
+        trig, n0, _ = p.triggers()
+        assert n0 == 0 and len(trig) == 0
+        p.filter(d)
+        full, n_all, _ = p.triggers()
+        part, n_part, st = p.triggers(cap=5)
+        assert n_all > 5 and n_part == n_all and len(part) == 5 and st == mf.MF_EOVERFLOW
+        assert np.array_equal(part, full[:5])
+        p.close()
