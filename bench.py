@@ -43,6 +43,9 @@ FP32_LANES_PER_SM = 128
 # names of the two filter kernels per plan implementation (mf_plan_stats.impl)
 # k_cols_h16 / k_cols_h16x2: k_cols with FP16 / FP16-pair output; k_rows_tc2: the split-product row pass
 KERNEL_NAMES = {2: ("k_cols", "k_rows"), 3: ("k_cols_h16", "k_rows_tc"), 4: ("k_cols_h16x2", "k_rows_tc2")}
+# the timed steps time every PROFILE_STRIDE-th launch pair of the filter kernels: the events between the two
+# passes of a timed pair keep the second kernel from launching early, so the others run undisturbed
+PROFILE_STRIDE = 8
 
 
 def measured_traffic(kernel, series_per_launch):
@@ -427,7 +430,7 @@ def uneven_main(args, rank, world, local):
     torch.cuda.synchronize()
     for p in plans:
         p.stats(reset=True)
-    plans[0].profile(True)
+    plans[0].profile(PROFILE_STRIDE)
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
@@ -486,6 +489,7 @@ def uneven_main(args, rank, world, local):
                 "bytes_convention": "the template's one-sided FD bins, read once and shared by both detectors of a "
                                     "segment (4,096 B per template-second at 2048 Hz, FP32 bank); time = the two "
                                     "passes per launch pair (CUDA events around the fused launches)",
+                "profile_stride": PROFILE_STRIDE,
                 "peak_kind": f"{hbm_kind} HBM copy bandwidth"}
     series_step = sum(n_tmpl[ci] * seg[ci]["n_seg"] * 2 for ci in range(n_cls))
     step_bytes = series_step * nb * 8 / 2
@@ -612,7 +616,7 @@ def main():
     # timed region: per-step CUDA events on the plans' stream, L2 flushed between steps
     for p in (h.p1, h.p2):
         p.stats(reset=True)
-        p.profile(True)
+        p.profile(PROFILE_STRIDE)
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
@@ -693,8 +697,9 @@ def main():
                 "series_per_launch": dp["series_per_launch"], "bytes_per_series": dp["bytes_per_series"],
                 "bytes_convention": "the template's one-sided FD bins, read once and shared by both detectors "
                                     "(FP32: 4,096 B per template-second at 2048 Hz); time = k_cols + k_rows per "
-                                    "launch pair (CUDA events on the plan's stream)",
-                "peak_kind": f"{hbm_kind} HBM copy bandwidth", "filters": pairs}
+                                    "launch pair (CUDA events on the plan's stream, every profile_stride-th pair "
+                                    "of the timed steps)",
+                "peak_kind": f"{hbm_kind} HBM copy bandwidth", "profile_stride": PROFILE_STRIDE, "filters": pairs}
     if kinds:
         dom = max(kinds, key=lambda d: d["ms"])
         per_launch_ms = dom["ms"] / dom["launches"]

@@ -292,7 +292,11 @@ typedef struct {
   int32_t batch;      /* templates per pass-1 / pass-2 launch pair */
 } mf_plan_stats;
 
-/* Turn event profiling of the filter kernels on (enable != 0) or off. */
+/* Event profiling of the filter kernels: enable = 0 off, 1 every template
+ * batch, k > 1 every k-th batch (counted across calls).  The events between
+ * the two kernels of a timed batch keep the second from launching early, so
+ * a stride keeps that cost to the sampled batches.  Errors: MF_EINVAL
+ * (enable < 0). */
 mf_status mf_profile(mf_plan_t plan, int enable);
 
 /* Read the counters into *out (synchronises the plan's stream); reset != 0

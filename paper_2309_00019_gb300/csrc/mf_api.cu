@@ -88,6 +88,8 @@ struct mf_plan_s {
   // instrumentation
   mf_plan_stats stats{};
   bool prof = false;
+  int prof_stride = 1;              // time every prof_stride-th launch pair
+  int64_t prof_count = 0;           // launch pairs since profiling was turned on
   std::vector<cudaEvent_t> ev;      // pool, 3 per sampled batch
   struct Sample {
     int e0;
@@ -692,7 +694,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
     a.pos0 = pos0;
     a.first_batch = pos0 == 0 ? 1 : 0;
     a.count = (int)std::min<int64_t>(p->batch, n_sel - pos0);
-    const bool prof = p->prof && (int)p->samples.size() < kProfBatches;
+    const bool prof = p->prof && p->prof_count++ % p->prof_stride == 0 && (int)p->samples.size() < kProfBatches;
     const int e0 = prof ? (int)p->samples.size() * 3 : 0;
     if (prof) cudaEventRecord(p->ev[e0], p->st);
     e = mf::launch_filter2_pass1(a, p->st);
@@ -716,6 +718,7 @@ mf_status mf_filter(mf_plan_t p, const void* dtilde, int64_t ld_dtilde, const in
 
 mf_status mf_profile(mf_plan_t p, int enable) {
   if (!p) return fail(p, MF_EINVAL, "mf_profile: null plan");
+  if (enable < 0) return fail(p, MF_EINVAL, "mf_profile: enable must be >= 0");
   if (enable && p->ev.empty()) {
     p->ev.resize(3 * kProfBatches);
     for (auto& e : p->ev) {
@@ -724,6 +727,8 @@ mf_status mf_profile(mf_plan_t p, int enable) {
     }
   }
   p->prof = enable != 0;
+  p->prof_stride = enable > 1 ? enable : 1;
+  p->prof_count = 0;
   return MF_OK;
 }
 
@@ -1176,7 +1181,8 @@ int filter_fused(mf_plan_s* const* plans, const void* const* dtilde, const int64
     ps.n_series = (int)ser;
     a.first_batch = first ? 1 : 0;
     first = false;
-    const bool prof = p0->prof && (int)p0->samples.size() < kProfBatches;
+    const bool prof =
+        p0->prof && p0->prof_count++ % p0->prof_stride == 0 && (int)p0->samples.size() < kProfBatches;
     const int e0 = prof ? (int)p0->samples.size() * 3 : 0;
     if (prof) cudaEventRecord(p0->ev[e0], st);
     if ((e = launch_filter2_fused(a, ps, scratch_map, st, prof ? p0->ev[e0 + 1] : nullptr)) != cudaSuccess)

@@ -378,6 +378,7 @@ class Plan:
         return n.value
 
     def profile(self, enable=True):
+        """mf_profile: False / 0 off, True / 1 every launch pair, k > 1 every k-th launch pair."""
         _check(self.h, self.lib.mf_profile(self.h, int(enable)))
 
     def stats(self, reset=False):

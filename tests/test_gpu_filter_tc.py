@@ -215,3 +215,31 @@ def test_tc_empty_subset_and_small_trigger_buffer(case):
         assert n_all > 5 and n_part == n_all and len(part) == 5 and st == mf.MF_EOVERFLOW
         assert np.array_equal(part, full[:5])
         p.close()
+
+
+def test_profiling_times_every_kth_launch_pair(case):
+    """mf_profile(k): the CUDA-event counters cover every k-th launch pair (counted across calls); profiling
+    changes no trigger."""
+    from paper_2309_00019_gb300 import mf
+
+    d = torch.from_numpy(case["fd"]).to(DEV)
+    p = mf.Plan(FS, N, 2, F_LOW, FS / 2, 4.0, int(FS), max_triggers=1 << 20)
+    p.set_psd(case["psd"])
+    p.load_bank(case["bank"])
+    p.set_intermediate(mf.MF_F16)
+    p.set_batch(1)  # 12 templates: 12 launch pairs per call
+    p.filter(d)
+    ref = p.triggers()[0].copy()
+    for k, want in ((1, 24), (2, 12), (5, 5)):
+        p.stats(reset=True)
+        p.profile(k)
+        p.filter(d)
+        p.filter(d)
+        st = p.stats(reset=True)
+        assert st["pass1_launches"] == st["pass2_launches"] == want, (k, st)
+        assert st["pass1_series"] == 2 * want and st["pass1_ms"] > 0 and st["pass2_ms"] > 0
+        assert np.array_equal(p.triggers()[0], ref)
+    p.profile(0)
+    with pytest.raises(mf.MFError):
+        p.profile(-1)
+    p.close()
