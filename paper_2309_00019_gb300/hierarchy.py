@@ -4,9 +4,11 @@ Stage 1 filters a coarse bank on the data decimated to the stage-1 rate;
 coincident two-detector triggers (zero lag and time-shifted) whose network SNR
 passes the follow-up threshold select coarse templates; stage 2 filters the
 union of their neighbourhoods in the fine bank at the full rate.  Every step
-runs in libmf's kernels on one CUDA stream; PyTorch only provides the device
-buffers and the stream.  The host waits once per step, to size stage 2 from
-the union count.
+runs in libmf's kernels on two CUDA streams, stage 1 on its own, ordered by
+events (the spectrum before stage 1, the coincidences before the union), so that
+the coincidences can be read back while stage 2 runs; PyTorch only provides the
+device buffers, the streams and the events.  The host waits once per step, to
+size stage 2 from the union count.
 """
 
 from __future__ import annotations
@@ -56,12 +58,14 @@ class Hierarchy:
         self.torch = torch
         self.hp = hp
         self.dev = torch.device(device)
-        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.dev)
-        sh = self.stream.cuda_stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.dev)  # the step's stream
+        self.stream1 = torch.cuda.Stream(device=self.dev)  # stage 1
+        self.ev_fd = torch.cuda.Event()  # the stage-2 spectrum is written
+        self.ev_co = torch.cuda.Event()  # stage 1 and its coincidences are done
         self.p2 = mf.Plan(hp.fs2, hp.n2, hp.n_det, hp.f_low, hp.fs2 / 2, hp.thr2, hp.window2,
-                          max_triggers=hp.max_trig2, stream=sh)
+                          max_triggers=hp.max_trig2, stream=self.stream.cuda_stream)
         self.p1 = mf.Plan(hp.fs1, hp.n1, hp.n_det, hp.f_low, hp.fs1 / 2, hp.thr1, hp.window1,
-                          max_triggers=hp.max_trig1, stream=sh)
+                          max_triggers=hp.max_trig1, stream=self.stream1.cuda_stream)
         self.p1.set_psd(psd1)
         self.p2.set_psd(psd2)
         self.n_coarse, self.n_fine = n_coarse, n_fine
@@ -93,16 +97,24 @@ class Hierarchy:
             plan.bank_set_rows(row0, rows, on_device=1)
 
     # -- one step ---------------------------------------------------------------
-    def run(self, strain=None):
-        """Whole hot path on device-resident strain [n_det, n2] (default: self.strain)."""
+    def _stage1(self, s):
+        """Spectrum (step stream), stage 1 and coincidences (stage-1 stream), union (step stream, waits)."""
         hp = self.hp
-        s = self.strain if strain is None else strain
         self.p2.strain_to_fd(s, self.d2, ld_strain=hp.n2, ld_dtilde=self.ld2)
+        self.ev_fd.record(self.stream)
+        self.stream1.wait_event(self.ev_fd)
         self.p1.decimate(self.d2, self.d1, ld_in=self.ld2, ld_out=self.ld1)
         self.p1.filter(self.d1, ld=self.ld1)
         self.p1.coincide(self.followed, self.shift1, hp.n_shifts, self.win1, hp.rho_c_thr,
                          max_coincs=hp.max_coincs)
+        self.ev_co.record(self.stream1)
+        self.stream.wait_event(self.ev_co)
         self.n_union = self.p2.nbhd_union(self.followed, self.subset)
+
+    def run(self, strain=None):
+        """Whole hot path on device-resident strain [n_det, n2] (default: self.strain); every step of it is
+        ordered on the step's stream (self.stream) by its end."""
+        self._stage1(self.strain if strain is None else strain)
         self.p2.filter(self.d2, subset=self.subset, n_subset=self.n_union, ld=self.ld2)
         return self.n_union
 
@@ -114,8 +126,9 @@ class Hierarchy:
         with self.torch.cuda.stream(self.stream):
             self.strain.copy_(strain_host, non_blocking=True)
         self.run()
-        trig2, n2, _ = self.p2.triggers(pinned=True)  # page-locked readback, valid until the next step
+        # stage 1's stream is idle by now: its coincidences are read (and ordered on the host) while stage 2 runs
         co, nco, _ = self.p1.coincs(pinned=True)
+        trig2, n2, _ = self.p2.triggers(pinned=True)  # page-locked readback, valid until the next step
         return trig2, co
 
     def td_seconds(self):
